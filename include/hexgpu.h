@@ -1,0 +1,215 @@
+/*
+ * hexgpu -- negacyclic NTT and element-wise modular arithmetic over RNS limbs
+ * on one NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * The operations are those of Intel HEXL (arXiv 2103.16400): the forward and
+ * inverse negacyclic number-theoretic transform over Z_q[X]/(X^N + 1)
+ * (Section 2.2: Cooley-Tukey forward with bit-reversed output, Gentleman-Sande
+ * inverse with N^-1 scaling, Harvey lazy butterflies, Shoup twiddle factors)
+ * and the element-wise kernels EltwiseAddMod, EltwiseMultMod, EltwiseFMAMod
+ * (Section 3, free-function API), batched over polynomials and RNS limbs
+ * (Section 4 describes the RNS form, in which limbs are independent).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Layout.    A batch of polynomials is a dense uint64 array
+ *             [n_polys][n_limbs][N]: limb l of polynomial p starts at
+ *             ptr + (p * n_limbs + l) * N.  Element-wise calls use the same
+ *             layout with a row length n instead of N.
+ *  Memory.    Arguments named d_* are device pointers that the caller owns
+ *             (for example torch tensor storage), 16-byte aligned.  Arguments
+ *             named h_* are host pointers, read during the call only.
+ *             A result may alias its operand exactly (in-place operation);
+ *             partial overlap is rejected.
+ *  Streams.   Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy
+ *             default stream) and the call returns without waiting for it.
+ *             Errors detected on the host are returned before anything is
+ *             enqueued; launch errors are returned as HX_ERR_CUDA.
+ *  Moduli.    q must be prime with q = 1 mod 2N for the transforms
+ *             (Section 2: q = 1 mod 2N), and below 2^62 (the Harvey
+ *             butterflies require q < beta/4 with beta = 2^64).  Limbs with
+ *             q < 2^30 run on 32-bit words (beta = 2^32).
+ *  Lazy ranges. input_mod_factor k promises every input value is in [0, k q);
+ *             output_mod_factor k returns values in [0, k q) that are
+ *             congruent to the exact result (Section 3, NTT class API).
+ *             Inputs outside the promised range give undefined results, as
+ *             in the paper.
+ *  Threads.   Calls may be made from several host threads; a plan may be used
+ *             by several streams at once but destroyed only when idle.
+ *  Errors.    Every call returns HX_OK (0) or a negative hx_status;
+ *             hx_strerror() names it.
+ */
+#ifndef HEXGPU_H
+#define HEXGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* hx_stream_t; /* same type as cudaStream_t */
+typedef struct hx_plan_s* hx_plan_t;
+typedef struct hx_batch_s* hx_batch_t;
+
+typedef enum hx_status {
+    HX_OK = 0,
+    HX_ERR_NULL = -1,         /* a required pointer is NULL */
+    HX_ERR_ALIGN = -2,        /* a device pointer is not 16-byte aligned */
+    HX_ERR_DEGREE = -3,       /* N is not a power of two in [2^10, 2^17] */
+    HX_ERR_MODULUS = -4,      /* q not prime, q != 1 mod 2N, or q out of range */
+    HX_ERR_ROOT = -5,         /* a supplied root is not a primitive 2N-th root */
+    HX_ERR_MOD_FACTOR = -6,   /* input/output mod factor not allowed */
+    HX_ERR_CUDA = -7,         /* a CUDA runtime call failed */
+    HX_ERR_ARG = -8,          /* another argument is out of range */
+    HX_ERR_OVERLAP = -9,      /* result and operand partially overlap */
+    HX_ERR_TIMEOUT = -10,     /* a device-side wait gave up */
+    HX_ERR_NOMEM = -11        /* device or host allocation failed */
+} hx_status;
+
+const char* hx_strerror(int status);
+
+/* Version of this ABI; bumps on any incompatible change. */
+int hx_abi_version(void);
+
+/* --------------------------------------------------------------------- plan
+ * A plan owns, in device memory, the per-limb tables that the paper's NTT
+ * class precomputes at construction (Section 3, "The NTT class performs
+ * pre-computation"): psi_rev (powers of psi in bit-reversed order, the
+ * Cooley-Tukey twiddles), psi^-1_rev (the Gentleman-Sande twiddles), the
+ * Shoup factor W' = floor(W beta / q) of each, N^-1 and its Shoup factor.
+ *
+ * hx_plan_create(out, N, h_moduli, n_limbs, h_roots)
+ *   N         transform length, a power of two in [2^10, 2^17].
+ *   h_moduli  host array of n_limbs primes, each q = 1 mod 2N and q < 2^62.
+ *   n_limbs   1 .. 4096.
+ *   h_roots   host array of n_limbs primitive 2N-th roots of unity (psi, one
+ *             per modulus) or NULL.  When NULL, psi is the numerically
+ *             smallest primitive 2N-th root of unity mod q (the paper leaves
+ *             psi open when none is given).
+ *   *out      receives the plan.  The plan allocates 32*N bytes of device
+ *             memory per limb on the current device, and is valid on that
+ *             device only.
+ *   Errors: HX_ERR_NULL, HX_ERR_DEGREE, HX_ERR_MODULUS, HX_ERR_ROOT,
+ *   HX_ERR_ARG, HX_ERR_NOMEM, HX_ERR_CUDA.
+ */
+int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli, uint32_t n_limbs,
+                   const uint64_t* h_roots);
+int hx_plan_destroy(hx_plan_t plan);
+
+/* Copies the plan's psi per limb into h_roots_out[n_limbs]. */
+int hx_plan_roots(hx_plan_t plan, uint64_t* h_roots_out);
+
+/* Plan shape: N, limb count and the device bytes the plan holds. */
+int hx_plan_info(hx_plan_t plan, uint64_t* N, uint32_t* n_limbs, uint64_t* device_bytes);
+
+/* ----------------------------------------------------------------- transforms
+ * hx_ntt_forward: forward negacyclic NTT of every limb of n_polys
+ *   polynomials (Section 2.2, Algorithm "Cooley-Tukey Radix-2 NTT" with the
+ *   Harvey butterfly): d_result[i] = sum_j d_operand[j] psi^((2 brv(i)+1) j)
+ *   mod q, output in bit-reversed order.
+ *   d_operand, d_result: [n_polys][plan n_limbs][N] uint64, equal or disjoint.
+ *   input_mod_factor in {1, 2, 4}; output_mod_factor in {1, 4}.
+ *
+ * hx_ntt_inverse: inverse negacyclic NTT (Algorithm "Gentleman-Sande Radix-2
+ *   InvNTT" with the Harvey inverse butterfly and the N^-1 scaling folded
+ *   into the last stage): bit-reversed input, standard-order output.
+ *   input_mod_factor in {1, 2}; output_mod_factor in {1, 2}.
+ *
+ * Both enqueue the transform on `stream`.  Errors: HX_ERR_NULL, HX_ERR_ALIGN,
+ * HX_ERR_ARG (n_polys == 0), HX_ERR_MOD_FACTOR, HX_ERR_OVERLAP, HX_ERR_CUDA.
+ */
+int hx_ntt_forward(hx_plan_t plan, uint64_t* d_result, const uint64_t* d_operand,
+                   uint32_t n_polys, uint32_t input_mod_factor, uint32_t output_mod_factor,
+                   hx_stream_t stream);
+int hx_ntt_inverse(hx_plan_t plan, uint64_t* d_result, const uint64_t* d_operand,
+                   uint32_t n_polys, uint32_t input_mod_factor, uint32_t output_mod_factor,
+                   hx_stream_t stream);
+
+/* In-place transforms of one polynomial's n_limbs limbs ([n_limbs][N] at
+ * d_ptr), the (ptr, N, q, n_limbs, input_mod_factor, output_mod_factor) form
+ * of the problem statement.  The plan for (N, moduli) is built on first use
+ * and cached (the first call for a new modulus set is therefore slow and
+ * allocates; call it once outside any stream capture).  Same errors as above
+ * plus those of hx_plan_create. */
+int hx_ntt_forward_raw(uint64_t* d_ptr, uint64_t N, const uint64_t* h_moduli, uint32_t n_limbs,
+                       uint32_t input_mod_factor, uint32_t output_mod_factor,
+                       hx_stream_t stream);
+int hx_ntt_inverse_raw(uint64_t* d_ptr, uint64_t N, const uint64_t* h_moduli, uint32_t n_limbs,
+                       uint32_t input_mod_factor, uint32_t output_mod_factor,
+                       hx_stream_t stream);
+
+/* --------------------------------------------------------------- element-wise
+ * All take rows of n elements in the [n_polys][n_limbs][n] layout; row
+ * (p, l) is reduced modulo h_moduli[l].  n >= 1 (any n: no multiple-of-8
+ * requirement, Section 3.3 handles the N mod 8 tail the same way).
+ *
+ * hx_eltwise_add_mod: r = (a + b) mod q; a, b in [0, q); q in [2, 2^63 - 1]
+ *   (Section 3, EltwiseAddMod).
+ * hx_eltwise_sub_mod: r = (a - b) mod q; a, b in [0, q); q in [2, 2^63 - 1].
+ * hx_eltwise_mult_mod: r = (a * b) mod q, a and b in [0, k q) for
+ *   k = input_mod_factor in {1, 2, 4}; q in [2, 2^62) with k q < 2^63
+ *   (Section 3.3, Algorithm "VectorVectorModMulAVX512Int": Barrett reduction
+ *   with Q = bitlen(q), L = 63 + Q).
+ * hx_eltwise_fma_mod: r = (a * s_l + d) mod q with one scalar s_l in [0, q)
+ *   per limb (h_scalars, host) and an optional addend d (NULL: none);
+ *   a, d in [0, k q), k = input_mod_factor in {1, 2, 4, 8}; q in [2, 2^61 - 1]
+ *   (Section 3.3, Algorithm "EltwiseFMAModAVX512").
+ * Outputs are in [0, q).  Errors: HX_ERR_NULL, HX_ERR_ALIGN, HX_ERR_ARG,
+ * HX_ERR_MODULUS, HX_ERR_MOD_FACTOR, HX_ERR_OVERLAP, HX_ERR_CUDA.
+ */
+int hx_eltwise_add_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* d_b, uint64_t n,
+                       const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
+                       hx_stream_t stream);
+int hx_eltwise_sub_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* d_b, uint64_t n,
+                       const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
+                       hx_stream_t stream);
+int hx_eltwise_mult_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* d_b, uint64_t n,
+                        const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
+                        uint32_t input_mod_factor, hx_stream_t stream);
+int hx_eltwise_fma_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* h_scalars,
+                       const uint64_t* d_addend, uint64_t n, const uint64_t* h_moduli,
+                       uint32_t n_limbs, uint32_t n_polys, uint32_t input_mod_factor,
+                       hx_stream_t stream);
+
+/* --------------------------------------------------------------- compositions
+ * hx_poly_mul: negacyclic product r = a * b in R_q per limb, composed as in
+ *   the paper's Listing 4: forward NTT of a and of b in place with output in
+ *   [0, 4q), EltwiseMultMod with input_mod_factor 4, inverse NTT to [0, q).
+ *   d_a and d_b are overwritten with their transforms; d_result may equal
+ *   d_a.  All [n_polys][plan n_limbs][N].
+ *
+ * hx_ciphertext_tensor: product of two degree-1 ciphertexts (a0, a1) and
+ *   (b0, b1) in coefficient form, followed by a scaled accumulation:
+ *     A_i, B_i = forward NTT of a_i, b_i (in place, output in [0, 4q))
+ *     d0 = A0 B0,  d1 = A0 B1 + A1 B0,  d2 = A1 B1   (element-wise mod q)
+ *     r_k = d_k * s_l + e_k mod q                    (EltwiseFMAMod)
+ *     out_k = inverse NTT of r_k, in [0, q).
+ *   The products, the sum and the scaling run in one fused element-wise
+ *   kernel; all steps are enqueued on `stream`.  e_k are in [0, q) (NTT
+ *   domain); h_scalars holds one s_l in [0, q) per limb.  The four inputs
+ *   are overwritten with their transforms; out_k must not alias any input.
+ */
+int hx_poly_mul(hx_plan_t plan, uint64_t* d_result, uint64_t* d_a, uint64_t* d_b,
+                uint32_t n_polys, hx_stream_t stream);
+int hx_ciphertext_tensor(hx_plan_t plan, uint64_t* d_out0, uint64_t* d_out1, uint64_t* d_out2,
+                         uint64_t* d_a0, uint64_t* d_a1, uint64_t* d_b0, uint64_t* d_b1,
+                         const uint64_t* h_scalars, const uint64_t* d_e0, const uint64_t* d_e1,
+                         const uint64_t* d_e2, uint32_t n_polys, hx_stream_t stream);
+
+/* Fused element-wise part of hx_ciphertext_tensor on its own: reads A0, A1,
+ * B0, B1 in [0, input_mod_factor q) (input_mod_factor in {1, 2, 4}) and e_k
+ * in [0, q), writes r_k in [0, q).  Rows of n elements, [n_polys][n_limbs][n]. */
+int hx_dyadic_tensor_fma(uint64_t* d_r0, uint64_t* d_r1, uint64_t* d_r2, const uint64_t* d_A0,
+                         const uint64_t* d_A1, const uint64_t* d_B0, const uint64_t* d_B1,
+                         const uint64_t* h_scalars, const uint64_t* d_e0, const uint64_t* d_e1,
+                         const uint64_t* d_e2, uint64_t n, const uint64_t* h_moduli,
+                         uint32_t n_limbs, uint32_t n_polys, uint32_t input_mod_factor,
+                         hx_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEXGPU_H */

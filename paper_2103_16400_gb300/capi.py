@@ -1,0 +1,219 @@
+"""Thin ctypes binding to libhexgpu.so, with the C ABI's own names.
+
+Argument marshalling only: device buffers are passed as raw pointers (a torch
+CUDA tensor's data_ptr(), or an int), host arrays are copied into ctypes
+arrays, streams default to torch's current stream.  Every computation runs
+in the CUDA library; there is no CPU path.  A non-zero status raises
+HexError carrying the library's own message.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhexgpu.so")
+
+U32, U64, I32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+VP = ctypes.c_void_p
+P64 = ctypes.POINTER(ctypes.c_uint64)
+
+# name -> argtypes (restype int unless listed in _RESTYPES)
+_SIGS = {
+    "hx_strerror": [I32],
+    "hx_abi_version": [],
+    "hx_plan_create": [ctypes.POINTER(VP), U64, P64, U32, P64],
+    "hx_plan_destroy": [VP],
+    "hx_plan_roots": [VP, P64],
+    "hx_plan_info": [VP, P64, ctypes.POINTER(U32), P64],
+    "hx_ntt_forward": [VP, VP, VP, U32, U32, U32, VP],
+    "hx_ntt_inverse": [VP, VP, VP, U32, U32, U32, VP],
+    "hx_ntt_forward_raw": [VP, U64, P64, U32, U32, U32, VP],
+    "hx_ntt_inverse_raw": [VP, U64, P64, U32, U32, U32, VP],
+    "hx_eltwise_add_mod": [VP, VP, VP, U64, P64, U32, U32, VP],
+    "hx_eltwise_sub_mod": [VP, VP, VP, U64, P64, U32, U32, VP],
+    "hx_eltwise_mult_mod": [VP, VP, VP, U64, P64, U32, U32, U32, VP],
+    "hx_eltwise_fma_mod": [VP, VP, P64, VP, U64, P64, U32, U32, U32, VP],
+    "hx_poly_mul": [VP, VP, VP, VP, U32, VP],
+    "hx_ciphertext_tensor": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, VP],
+    "hx_dyadic_tensor_fma": [VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U64, P64, U32, U32,
+                             U32, VP],
+}
+_RESTYPES = {"hx_strerror": ctypes.c_char_p}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class HexError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn}: {msg} (status {status})")
+        self.status = status
+
+
+def load():
+    """Load the CUDA library; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"libhexgpu.so is not built ({LIB_PATH}); run "
+                    "`python -m paper_2103_16400_gb300.build` (needs nvcc)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = _RESTYPES.get(name, I32)
+            _lib = L
+    return _lib
+
+
+def exported_symbols() -> Sequence[str]:
+    return list(_SIGS)
+
+
+def _check(fn: str, st: int):
+    if st != 0:
+        msg = load().hx_strerror(st).decode()
+        raise HexError(fn, st, msg)
+
+
+def ptr(x) -> Optional[int]:
+    """Device pointer of a torch tensor (or an int / None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def host_u64(values) -> ctypes.Array:
+    vals = [int(v) for v in values]
+    return (ctypes.c_uint64 * len(vals))(*vals)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# --------------------------------------------------------------------- plans
+class Plan:
+    """Owns an hx_plan_t: device twiddle tables for (N, moduli)."""
+
+    def __init__(self, N: int, moduli: Sequence[int], roots: Optional[Sequence[int]] = None):
+        L = load()
+        h = VP()
+        mod = host_u64(moduli)
+        rts = host_u64(roots) if roots is not None else None
+        _check("hx_plan_create", L.hx_plan_create(ctypes.byref(h), N, mod, len(moduli), rts))
+        self.handle = h.value
+        self.N = N
+        self.moduli = [int(q) for q in moduli]
+        self.n_limbs = len(moduli)
+
+    def roots(self):
+        out = (ctypes.c_uint64 * self.n_limbs)()
+        _check("hx_plan_roots", load().hx_plan_roots(self.handle, out))
+        return [int(x) for x in out]
+
+    def info(self):
+        N, nl, b = U64(), U32(), U64()
+        _check("hx_plan_info", load().hx_plan_info(self.handle, ctypes.byref(N),
+                                                   ctypes.byref(nl), ctypes.byref(b)))
+        return N.value, nl.value, b.value
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            _check("hx_plan_destroy", load().hx_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _h(plan):
+    return plan.handle if isinstance(plan, Plan) else plan
+
+
+# ------------------------------------------------------------- entry points
+def hx_ntt_forward(plan, result, operand, n_polys: int, input_mod_factor: int = 1,
+                   output_mod_factor: int = 1, stream=None):
+    _check("hx_ntt_forward", load().hx_ntt_forward(
+        _h(plan), ptr(result), ptr(operand), n_polys, input_mod_factor, output_mod_factor,
+        _stream(stream)))
+
+
+def hx_ntt_inverse(plan, result, operand, n_polys: int, input_mod_factor: int = 1,
+                   output_mod_factor: int = 1, stream=None):
+    _check("hx_ntt_inverse", load().hx_ntt_inverse(
+        _h(plan), ptr(result), ptr(operand), n_polys, input_mod_factor, output_mod_factor,
+        _stream(stream)))
+
+
+def hx_ntt_forward_raw(data, N: int, moduli, input_mod_factor=1, output_mod_factor=1,
+                       stream=None):
+    _check("hx_ntt_forward_raw", load().hx_ntt_forward_raw(
+        ptr(data), N, host_u64(moduli), len(moduli), input_mod_factor, output_mod_factor,
+        _stream(stream)))
+
+
+def hx_ntt_inverse_raw(data, N: int, moduli, input_mod_factor=1, output_mod_factor=1,
+                       stream=None):
+    _check("hx_ntt_inverse_raw", load().hx_ntt_inverse_raw(
+        ptr(data), N, host_u64(moduli), len(moduli), input_mod_factor, output_mod_factor,
+        _stream(stream)))
+
+
+def hx_eltwise_add_mod(result, a, b, n: int, moduli, n_polys: int = 1, stream=None):
+    _check("hx_eltwise_add_mod", load().hx_eltwise_add_mod(
+        ptr(result), ptr(a), ptr(b), n, host_u64(moduli), len(moduli), n_polys, _stream(stream)))
+
+
+def hx_eltwise_sub_mod(result, a, b, n: int, moduli, n_polys: int = 1, stream=None):
+    _check("hx_eltwise_sub_mod", load().hx_eltwise_sub_mod(
+        ptr(result), ptr(a), ptr(b), n, host_u64(moduli), len(moduli), n_polys, _stream(stream)))
+
+
+def hx_eltwise_mult_mod(result, a, b, n: int, moduli, n_polys: int = 1,
+                        input_mod_factor: int = 1, stream=None):
+    _check("hx_eltwise_mult_mod", load().hx_eltwise_mult_mod(
+        ptr(result), ptr(a), ptr(b), n, host_u64(moduli), len(moduli), n_polys,
+        input_mod_factor, _stream(stream)))
+
+
+def hx_eltwise_fma_mod(result, a, scalars, addend, n: int, moduli, n_polys: int = 1,
+                       input_mod_factor: int = 1, stream=None):
+    _check("hx_eltwise_fma_mod", load().hx_eltwise_fma_mod(
+        ptr(result), ptr(a), host_u64(scalars), ptr(addend), n, host_u64(moduli), len(moduli),
+        n_polys, input_mod_factor, _stream(stream)))
+
+
+def hx_poly_mul(plan, result, a, b, n_polys: int, stream=None):
+    _check("hx_poly_mul", load().hx_poly_mul(_h(plan), ptr(result), ptr(a), ptr(b), n_polys,
+                                             _stream(stream)))
+
+
+def hx_ciphertext_tensor(plan, out0, out1, out2, a0, a1, b0, b1, scalars, e0, e1, e2,
+                         n_polys: int, stream=None):
+    _check("hx_ciphertext_tensor", load().hx_ciphertext_tensor(
+        _h(plan), ptr(out0), ptr(out1), ptr(out2), ptr(a0), ptr(a1), ptr(b0), ptr(b1),
+        host_u64(scalars), ptr(e0), ptr(e1), ptr(e2), n_polys, _stream(stream)))
+
+
+def hx_dyadic_tensor_fma(r0, r1, r2, A0, A1, B0, B1, scalars, e0, e1, e2, n: int, moduli,
+                         n_polys: int = 1, input_mod_factor: int = 1, stream=None):
+    _check("hx_dyadic_tensor_fma", load().hx_dyadic_tensor_fma(
+        ptr(r0), ptr(r1), ptr(r2), ptr(A0), ptr(A1), ptr(B0), ptr(B1), host_u64(scalars),
+        ptr(e0), ptr(e1), ptr(e2), n, host_u64(moduli), len(moduli), n_polys,
+        input_mod_factor, _stream(stream)))

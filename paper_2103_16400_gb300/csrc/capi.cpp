@@ -1,0 +1,274 @@
+// extern "C" entry points of libhexgpu: argument validation, then dispatch to
+// the kernels.  Declarations and their documentation are in include/hexgpu.h.
+#include <string.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+
+#include "hx_internal.h"
+
+using namespace hx;
+
+namespace {
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// [a, a + bytes) and [b, b + bytes) overlap without being the same range
+bool partial_overlap(const void* a, const void* b, uint64_t bytes) {
+    if (!a || !b || a == b) return false;
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return HX_OK;
+    if (e == cudaErrorMemoryAllocation) return HX_ERR_NOMEM;
+    return HX_ERR_CUDA;
+}
+
+int check_ntt(hx_plan_t plan, const uint64_t* r, const uint64_t* x, uint32_t n_polys,
+              uint32_t in_mf, uint32_t out_mf, bool fwd) {
+    if (!plan || !r || !x) return HX_ERR_NULL;
+    if (!aligned16(r) || !aligned16(x)) return HX_ERR_ALIGN;
+    if (n_polys == 0 || (uint64_t)n_polys * plan->n_limbs > (1ull << 31) / 1) return HX_ERR_ARG;
+    if (fwd) {
+        if (!(in_mf == 1 || in_mf == 2 || in_mf == 4)) return HX_ERR_MOD_FACTOR;
+        if (!(out_mf == 1 || out_mf == 4)) return HX_ERR_MOD_FACTOR;
+    } else {
+        if (!(in_mf == 1 || in_mf == 2)) return HX_ERR_MOD_FACTOR;
+        if (!(out_mf == 1 || out_mf == 2)) return HX_ERR_MOD_FACTOR;
+    }
+    const uint64_t bytes = (uint64_t)n_polys * plan->n_limbs * plan->N * 8;
+    if (partial_overlap(r, x, bytes)) return HX_ERR_OVERLAP;
+    return HX_OK;
+}
+
+int check_elt(const uint64_t* r, const uint64_t* a, const uint64_t* b, bool b_required, uint64_t n,
+              const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys) {
+    if (!r || !a || !h_moduli || (b_required && !b)) return HX_ERR_NULL;
+    if (!aligned16(r) || !aligned16(a) || (b && !aligned16(b))) return HX_ERR_ALIGN;
+    if (n == 0 || n_limbs == 0 || n_polys == 0) return HX_ERR_ARG;
+    const uint64_t bytes = n * n_limbs * n_polys * 8;
+    if (partial_overlap(r, a, bytes) || partial_overlap(r, b, bytes)) return HX_ERR_OVERLAP;
+    return HX_OK;
+}
+
+struct RawKey {
+    int device;
+    uint64_t N;
+    std::vector<uint64_t> moduli;
+    bool operator<(const RawKey& o) const {
+        return std::tie(device, N, moduli) < std::tie(o.device, o.N, o.moduli);
+    }
+};
+
+std::mutex g_raw_mu;
+std::map<RawKey, hx_plan_t>* g_raw_plans = nullptr;
+
+int raw_plan(uint64_t N, const uint64_t* h_moduli, uint32_t n_limbs, hx_plan_t* out) {
+    if (!h_moduli) return HX_ERR_NULL;
+    if (n_limbs == 0) return HX_ERR_ARG;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    RawKey key{dev, N, std::vector<uint64_t>(h_moduli, h_moduli + n_limbs)};
+    std::lock_guard<std::mutex> g(g_raw_mu);
+    if (!g_raw_plans) g_raw_plans = new std::map<RawKey, hx_plan_t>();
+    auto it = g_raw_plans->find(key);
+    if (it != g_raw_plans->end()) {
+        *out = it->second;
+        return HX_OK;
+    }
+    hx_plan_t p = nullptr;
+    int st = hx_plan_create(&p, N, h_moduli, n_limbs, nullptr);
+    if (st != HX_OK) return st;
+    (*g_raw_plans)[key] = p;
+    *out = p;
+    return HX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hx_strerror(int s) {
+    switch (s) {
+        case HX_OK: return "success";
+        case HX_ERR_NULL: return "a required pointer is NULL";
+        case HX_ERR_ALIGN: return "a device pointer is not 16-byte aligned";
+        case HX_ERR_DEGREE: return "N is not a power of two in [2^10, 2^17]";
+        case HX_ERR_MODULUS: return "modulus not prime, not 1 mod 2N, or out of range";
+        case HX_ERR_ROOT: return "supplied root is not a primitive 2N-th root of unity";
+        case HX_ERR_MOD_FACTOR: return "input/output mod factor not allowed";
+        case HX_ERR_CUDA: return "CUDA runtime error";
+        case HX_ERR_ARG: return "argument out of range";
+        case HX_ERR_OVERLAP: return "result and operand partially overlap";
+        case HX_ERR_TIMEOUT: return "device-side wait timed out";
+        case HX_ERR_NOMEM: return "allocation failed";
+        default: return "unknown status";
+    }
+}
+
+int hx_abi_version(void) { return 1; }
+
+int hx_ntt_forward(hx_plan_t plan, uint64_t* r, const uint64_t* x, uint32_t n_polys,
+                   uint32_t in_mf, uint32_t out_mf, hx_stream_t stream) {
+    int st = check_ntt(plan, r, x, n_polys, in_mf, out_mf, true);
+    if (st != HX_OK) return st;
+    return cuda_status(launch_ntt(plan, r, x, n_polys, true, in_mf, out_mf, plan->cfg,
+                                  (cudaStream_t)stream));
+}
+
+int hx_ntt_inverse(hx_plan_t plan, uint64_t* r, const uint64_t* x, uint32_t n_polys,
+                   uint32_t in_mf, uint32_t out_mf, hx_stream_t stream) {
+    int st = check_ntt(plan, r, x, n_polys, in_mf, out_mf, false);
+    if (st != HX_OK) return st;
+    return cuda_status(launch_ntt(plan, r, x, n_polys, false, in_mf, out_mf, plan->cfg,
+                                  (cudaStream_t)stream));
+}
+
+int hx_ntt_forward_raw(uint64_t* d_ptr, uint64_t N, const uint64_t* h_moduli, uint32_t n_limbs,
+                       uint32_t in_mf, uint32_t out_mf, hx_stream_t stream) {
+    hx_plan_t p = nullptr;
+    int st = raw_plan(N, h_moduli, n_limbs, &p);
+    if (st != HX_OK) return st;
+    return hx_ntt_forward(p, d_ptr, d_ptr, 1, in_mf, out_mf, stream);
+}
+
+int hx_ntt_inverse_raw(uint64_t* d_ptr, uint64_t N, const uint64_t* h_moduli, uint32_t n_limbs,
+                       uint32_t in_mf, uint32_t out_mf, hx_stream_t stream) {
+    hx_plan_t p = nullptr;
+    int st = raw_plan(N, h_moduli, n_limbs, &p);
+    if (st != HX_OK) return st;
+    return hx_ntt_inverse(p, d_ptr, d_ptr, 1, in_mf, out_mf, stream);
+}
+
+static int check_moduli(const uint64_t* h_moduli, uint32_t n_limbs, uint64_t qmax, uint64_t qmin) {
+    for (uint32_t l = 0; l < n_limbs; ++l)
+        if (h_moduli[l] < qmin || h_moduli[l] > qmax) return HX_ERR_MODULUS;
+    return HX_OK;
+}
+
+int hx_eltwise_add_mod(uint64_t* r, const uint64_t* a, const uint64_t* b, uint64_t n,
+                       const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
+                       hx_stream_t stream) {
+    int st = check_elt(r, a, b, true, n, h_moduli, n_limbs, n_polys);
+    if (st != HX_OK) return st;
+    if ((st = check_moduli(h_moduli, n_limbs, (1ull << 63) - 1, 2)) != HX_OK) return st;
+    return cuda_status(launch_eltwise(ELT_ADD, r, a, b, nullptr, n, h_moduli, n_limbs, n_polys, 1,
+                                      (cudaStream_t)stream));
+}
+
+int hx_eltwise_sub_mod(uint64_t* r, const uint64_t* a, const uint64_t* b, uint64_t n,
+                       const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
+                       hx_stream_t stream) {
+    int st = check_elt(r, a, b, true, n, h_moduli, n_limbs, n_polys);
+    if (st != HX_OK) return st;
+    if ((st = check_moduli(h_moduli, n_limbs, (1ull << 63) - 1, 2)) != HX_OK) return st;
+    return cuda_status(launch_eltwise(ELT_SUB, r, a, b, nullptr, n, h_moduli, n_limbs, n_polys, 1,
+                                      (cudaStream_t)stream));
+}
+
+int hx_eltwise_mult_mod(uint64_t* r, const uint64_t* a, const uint64_t* b, uint64_t n,
+                        const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
+                        uint32_t in_mf, hx_stream_t stream) {
+    int st = check_elt(r, a, b, true, n, h_moduli, n_limbs, n_polys);
+    if (st != HX_OK) return st;
+    if (!(in_mf == 1 || in_mf == 2 || in_mf == 4)) return HX_ERR_MOD_FACTOR;
+    if ((st = check_moduli(h_moduli, n_limbs, (1ull << 62) - 1, 3)) != HX_OK) return st;
+    for (uint32_t l = 0; l < n_limbs; ++l) {
+        const uint64_t q = h_moduli[l];
+        if ((q & (q - 1)) == 0) return HX_ERR_MODULUS;        // Barrett k needs q > 2^(Q-1)
+        if ((unsigned __int128)in_mf * q >= ((unsigned __int128)1 << 63)) return HX_ERR_MOD_FACTOR;
+    }
+    return cuda_status(launch_eltwise(ELT_MULT, r, a, b, nullptr, n, h_moduli, n_limbs, n_polys,
+                                      in_mf, (cudaStream_t)stream));
+}
+
+int hx_eltwise_fma_mod(uint64_t* r, const uint64_t* a, const uint64_t* h_scalars,
+                       const uint64_t* d_addend, uint64_t n, const uint64_t* h_moduli,
+                       uint32_t n_limbs, uint32_t n_polys, uint32_t in_mf, hx_stream_t stream) {
+    if (!h_scalars) return HX_ERR_NULL;
+    int st = check_elt(r, a, d_addend, false, n, h_moduli, n_limbs, n_polys);
+    if (st != HX_OK) return st;
+    if (!(in_mf == 1 || in_mf == 2 || in_mf == 4 || in_mf == 8)) return HX_ERR_MOD_FACTOR;
+    if ((st = check_moduli(h_moduli, n_limbs, (1ull << 61) - 1, 2)) != HX_OK) return st;
+    for (uint32_t l = 0; l < n_limbs; ++l)
+        if (h_scalars[l] >= h_moduli[l]) return HX_ERR_ARG;
+    return cuda_status(launch_eltwise(ELT_FMA, r, a, d_addend, h_scalars, n, h_moduli, n_limbs,
+                                      n_polys, in_mf, (cudaStream_t)stream));
+}
+
+int hx_dyadic_tensor_fma(uint64_t* r0, uint64_t* r1, uint64_t* r2, const uint64_t* A0,
+                         const uint64_t* A1, const uint64_t* B0, const uint64_t* B1,
+                         const uint64_t* h_scalars, const uint64_t* e0, const uint64_t* e1,
+                         const uint64_t* e2, uint64_t n, const uint64_t* h_moduli,
+                         uint32_t n_limbs, uint32_t n_polys, uint32_t in_mf, hx_stream_t stream) {
+    if (!r0 || !r1 || !r2 || !A0 || !A1 || !B0 || !B1 || !h_scalars || !e0 || !e1 || !e2 ||
+        !h_moduli)
+        return HX_ERR_NULL;
+    if (n == 0 || n_limbs == 0 || n_polys == 0) return HX_ERR_ARG;
+    if (!(in_mf == 1 || in_mf == 2 || in_mf == 4)) return HX_ERR_MOD_FACTOR;
+    int st = check_moduli(h_moduli, n_limbs, (1ull << 61) - 1, 3);
+    if (st != HX_OK) return st;
+    for (uint32_t l = 0; l < n_limbs; ++l) {
+        const uint64_t q = h_moduli[l];
+        if ((q & (q - 1)) == 0) return HX_ERR_MODULUS;
+        if (h_scalars[l] >= q) return HX_ERR_ARG;
+    }
+    const uint64_t bytes = n * n_limbs * n_polys * 8;
+    const uint64_t* ins[7] = {A0, A1, B0, B1, e0, e1, e2};
+    uint64_t* outs[3] = {r0, r1, r2};
+    for (auto o : outs) {
+        if (!aligned16(o)) return HX_ERR_ALIGN;
+        for (auto i : ins) {
+            // outputs may not alias inputs at all: each output element is
+            // written after reading several inputs at the same index
+            const uintptr_t x = (uintptr_t)o, y = (uintptr_t)i;
+            if (x < y + bytes && y < x + bytes) return HX_ERR_OVERLAP;
+        }
+    }
+    for (auto i : ins)
+        if (!aligned16(i)) return HX_ERR_ALIGN;
+    return cuda_status(launch_tensor_fma(r0, r1, r2, A0, A1, B0, B1, h_scalars, e0, e1, e2, n,
+                                         h_moduli, n_limbs, n_polys, in_mf, (cudaStream_t)stream));
+}
+
+int hx_poly_mul(hx_plan_t plan, uint64_t* r, uint64_t* a, uint64_t* b, uint32_t n_polys,
+                hx_stream_t stream) {
+    if (!plan || !r || !a || !b) return HX_ERR_NULL;
+    const uint64_t bytes = (uint64_t)n_polys * plan->n_limbs * plan->N * 8;
+    if (a == b || partial_overlap(a, b, bytes)) return HX_ERR_OVERLAP;
+    if (r != a && r != b && (partial_overlap(r, a, bytes) || partial_overlap(r, b, bytes)))
+        return HX_ERR_OVERLAP;
+    int st = hx_ntt_forward(plan, a, a, n_polys, 1, 4, stream);
+    if (st != HX_OK) return st;
+    if ((st = hx_ntt_forward(plan, b, b, n_polys, 1, 4, stream)) != HX_OK) return st;
+    st = cuda_status(launch_eltwise(ELT_MULT, r, a, b, nullptr, plan->N, plan->moduli.data(),
+                                    plan->n_limbs, n_polys, 4, (cudaStream_t)stream));
+    if (st != HX_OK) return st;
+    return hx_ntt_inverse(plan, r, r, n_polys, 1, 1, stream);
+}
+
+int hx_ciphertext_tensor(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* o2, uint64_t* a0,
+                         uint64_t* a1, uint64_t* b0, uint64_t* b1, const uint64_t* h_scalars,
+                         const uint64_t* e0, const uint64_t* e1, const uint64_t* e2,
+                         uint32_t n_polys, hx_stream_t stream) {
+    if (!plan || !o0 || !o1 || !o2 || !a0 || !a1 || !b0 || !b1) return HX_ERR_NULL;
+    for (uint32_t l = 0; l < plan->n_limbs; ++l)
+        if (plan->moduli[l] >= (1ull << 61)) return HX_ERR_MODULUS;
+    int st;
+    uint64_t* ins[4] = {a0, a1, b0, b1};
+    for (auto x : ins)
+        if ((st = hx_ntt_forward(plan, x, x, n_polys, 1, 4, stream)) != HX_OK) return st;
+    st = hx_dyadic_tensor_fma(o0, o1, o2, a0, a1, b0, b1, h_scalars, e0, e1, e2, plan->N,
+                              plan->moduli.data(), plan->n_limbs, n_polys, 4, stream);
+    if (st != HX_OK) return st;
+    uint64_t* outs[3] = {o0, o1, o2};
+    for (auto x : outs)
+        if ((st = hx_ntt_inverse(plan, x, x, n_polys, 1, 1, stream)) != HX_OK) return st;
+    return HX_OK;
+}
+
+}  // extern "C"

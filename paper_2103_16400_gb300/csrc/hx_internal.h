@@ -1,0 +1,78 @@
+// Internal declarations shared by the translation units of libhexgpu.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/hexgpu.h"
+
+namespace hx {
+
+// Per-limb constants resident on the device (one array per plan).
+struct LimbDev {
+    uint64_t q;
+    uint64_t two_q;
+    const ulonglong2* fwd;  // [N] {W, W'}: W = psi^brv(k), W' its Shoup factor
+    const ulonglong2* inv;  // [N] {W, W'}: W = psi^-brv(k)
+    uint64_t ninv, ninv_p;      // N^-1 and its Shoup factor
+    uint64_t ninv_w, ninv_w_p;  // N^-1 * psi^-brv(1) and its Shoup factor
+    uint32_t narrow;            // 1: q < 2^30, 32-bit words, beta = 2^32
+    uint32_t pad;
+};
+
+// One pass of a transform: CT stages [s0, s0 + K) on tiles of
+// 2^logGb (top-index values) x 2^K x 2^logGc (low-index values) elements.
+struct PassCfg {
+    int s0, K, logGb, logGc, logR;
+};
+
+struct NttCfg {
+    int npass;
+    PassCfg pass[2];
+};
+
+}  // namespace hx
+
+struct hx_plan_s {
+    uint64_t N = 0;
+    int logN = 0;
+    uint32_t n_limbs = 0;
+    int device = 0;
+    std::vector<uint64_t> moduli, roots;
+    void* d_tables = nullptr;       // fwd then inv tables, all limbs
+    hx::LimbDev* d_limbs = nullptr;
+    std::vector<hx::LimbDev> h_limbs;
+    uint64_t device_bytes = 0;
+    hx::NttCfg cfg{};
+};
+
+namespace hx {
+
+// plan.cpp
+bool is_prime_u64(uint64_t n);
+uint64_t powmod_u64(uint64_t a, uint64_t e, uint64_t q);
+uint64_t min_primitive_root(uint64_t N, uint64_t q);
+NttCfg default_cfg(int logN);
+
+// ntt.cu
+cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
+                       uint32_t n_polys, bool forward, uint32_t in_mf, uint32_t out_mf,
+                       const NttCfg& cfg, cudaStream_t stream);
+bool cfg_supported(int logN, const NttCfg& cfg);
+
+// eltwise.cu
+enum EltOp { ELT_ADD = 0, ELT_SUB = 1, ELT_MULT = 2, ELT_FMA = 3 };
+cudaError_t launch_eltwise(int op, uint64_t* r, const uint64_t* a, const uint64_t* b,
+                           const uint64_t* h_scalars, uint64_t n, const uint64_t* h_moduli,
+                           uint32_t n_limbs, uint32_t n_polys, uint32_t in_mf,
+                           cudaStream_t stream);
+cudaError_t launch_tensor_fma(uint64_t* r0, uint64_t* r1, uint64_t* r2, const uint64_t* A0,
+                              const uint64_t* A1, const uint64_t* B0, const uint64_t* B1,
+                              const uint64_t* h_scalars, const uint64_t* e0, const uint64_t* e1,
+                              const uint64_t* e2, uint64_t n, const uint64_t* h_moduli,
+                              uint32_t n_limbs, uint32_t n_polys, uint32_t in_mf,
+                              cudaStream_t stream);
+
+}  // namespace hx

@@ -1,0 +1,237 @@
+// Plan construction: the precomputation that the paper's NTT class performs
+// at initialisation (Section 3: roots of unity and their precomputed
+// factors), done once per (N, moduli) on the host and uploaded to HBM.
+//
+// Tables per limb (Section 2.2):
+//   fwd[k] = {psi^brv(k), floor(psi^brv(k) * beta / q)}    Cooley-Tukey twiddles
+//   inv[k] = {psi^-brv(k), floor(psi^-brv(k) * beta / q)}  Gentleman-Sande twiddles
+// with beta = 2^64 for wide limbs and 2^32 for narrow limbs (q < 2^30), the
+// Shoup factor W' of the Harvey butterflies.  Entry 0 is never read; it holds 1.
+#include <string.h>
+
+#include <algorithm>
+#include <thread>
+
+#include "hx_internal.h"
+
+typedef unsigned __int128 u128;
+
+namespace hx {
+
+static inline uint64_t mulmod(uint64_t a, uint64_t b, uint64_t q) {
+    return (uint64_t)(((u128)a * b) % q);
+}
+
+uint64_t powmod_u64(uint64_t a, uint64_t e, uint64_t q) {
+    uint64_t r = 1 % q;
+    a %= q;
+    while (e) {
+        if (e & 1) r = mulmod(r, a, q);
+        a = mulmod(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+
+// Deterministic Miller-Rabin; these twelve bases decide every n < 3.3e24.
+bool is_prime_u64(uint64_t n) {
+    static const uint64_t B[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (uint64_t p : B)
+        if (n % p == 0) return n == p;
+    uint64_t d = n - 1;
+    int s = 0;
+    while (!(d & 1)) { d >>= 1; ++s; }
+    for (uint64_t a : B) {
+        uint64_t x = powmod_u64(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool composite = true;
+        for (int r = 1; r < s && composite; ++r) {
+            x = mulmod(x, x, n);
+            if (x == n - 1) composite = false;
+        }
+        if (composite) return false;
+    }
+    return true;
+}
+
+// Smallest primitive 2N-th root of unity mod prime q = 1 mod 2N: an element
+// of multiplicative order 2N (N a power of two) is exactly one with x^N = -1.
+// A quadratic non-residue g gives h = g^((q-1)/2N) with h^N = -1; the 2N-th
+// primitive roots are then the odd powers of h.
+uint64_t min_primitive_root(uint64_t N, uint64_t q) {
+    uint64_t h = 0;
+    for (uint64_t g = 2; g < q && g < (1ull << 24); ++g) {
+        uint64_t c = powmod_u64(g, (q - 1) / (2 * N), q);
+        if (powmod_u64(c, N, q) == q - 1) { h = c; break; }
+    }
+    if (!h) return 0;
+    uint64_t h2 = mulmod(h, h, q), x = h, best = h;
+    for (uint64_t k = 1; k < N; ++k) {
+        x = mulmod(x, h2, q);
+        best = std::min(best, x);
+    }
+    return best;
+}
+
+static inline uint64_t bitrev(uint64_t i, int logn) {
+    uint64_t r = 0;
+    for (int b = 0; b < logn; ++b) { r = (r << 1) | (i & 1); i >>= 1; }
+    return r;
+}
+
+static inline uint64_t shoup(uint64_t w, uint64_t q, bool narrow) {
+    return narrow ? (uint64_t)(((uint64_t)w << 32) / q) : (uint64_t)(((u128)w << 64) / q);
+}
+
+// Fill one limb's tables (host staging buffers of N pairs each).
+static void fill_limb(uint64_t N, int logN, uint64_t q, uint64_t psi, ulonglong2* fwd,
+                      ulonglong2* inv, LimbDev* ld) {
+    const bool narrow = q < (1ull << 30);
+    const uint64_t psi_inv = powmod_u64(psi, q - 2, q);
+    std::vector<uint64_t> pw(N), pwi(N);
+    pw[0] = pwi[0] = 1;
+    for (uint64_t i = 1; i < N; ++i) {
+        pw[i] = mulmod(pw[i - 1], psi, q);
+        pwi[i] = mulmod(pwi[i - 1], psi_inv, q);
+    }
+    for (uint64_t k = 0; k < N; ++k) {
+        uint64_t r = bitrev(k, logN);
+        uint64_t w = k ? pw[r] : 1, wi = k ? pwi[r] : 1;
+        fwd[k] = make_ulonglong2(w, shoup(w, q, narrow));
+        inv[k] = make_ulonglong2(wi, shoup(wi, q, narrow));
+    }
+    uint64_t ninv = powmod_u64(N % q, q - 2, q);
+    uint64_t ninv_w = mulmod(ninv, inv[1].x, q);
+    ld->q = q;
+    ld->two_q = 2 * q;
+    ld->ninv = ninv;
+    ld->ninv_p = shoup(ninv, q, narrow);
+    ld->ninv_w = ninv_w;
+    ld->ninv_w_p = shoup(ninv_w, q, narrow);
+    ld->narrow = narrow ? 1u : 0u;
+    ld->pad = 0;
+}
+
+NttCfg default_cfg(int logN) {
+    NttCfg c{};
+    if (logN <= 13) {
+        c.npass = 1;
+        c.pass[0] = PassCfg{0, logN, 0, 0, logN <= 12 ? 3 : 4};
+    } else {
+        int K1 = logN / 2, K2 = logN - K1;
+        c.npass = 2;
+        c.pass[0] = PassCfg{0, K1, 0, 4, 3};
+        int logGb = std::max(0, 12 - K2);
+        c.pass[1] = PassCfg{K1, K2, std::min(logGb, K1), 0, 3};
+    }
+    return c;
+}
+
+}  // namespace hx
+
+using namespace hx;
+
+extern "C" int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli,
+                              uint32_t n_limbs, const uint64_t* h_roots) {
+    if (!out || !h_moduli) return HX_ERR_NULL;
+    *out = nullptr;
+    if (N < 1024 || N > (1u << 17) || (N & (N - 1))) return HX_ERR_DEGREE;
+    if (n_limbs == 0 || n_limbs > 4096) return HX_ERR_ARG;
+    int logN = 0;
+    while ((1ull << logN) < N) ++logN;
+    std::vector<uint64_t> roots(n_limbs);
+    for (uint32_t l = 0; l < n_limbs; ++l) {
+        uint64_t q = h_moduli[l];
+        if (q < 3 || q >= (1ull << 62) || (q - 1) % (2 * N) != 0 || !is_prime_u64(q))
+            return HX_ERR_MODULUS;
+        if (h_roots) {
+            uint64_t r = h_roots[l];
+            if (r == 0 || r >= q || powmod_u64(r, N, q) != q - 1) return HX_ERR_ROOT;
+            roots[l] = r;
+        } else {
+            roots[l] = min_primitive_root(N, q);
+            if (!roots[l]) return HX_ERR_MODULUS;
+        }
+    }
+    hx_plan_s* p = new (std::nothrow) hx_plan_s();
+    if (!p) return HX_ERR_NOMEM;
+    p->N = N;
+    p->logN = logN;
+    p->n_limbs = n_limbs;
+    p->moduli.assign(h_moduli, h_moduli + n_limbs);
+    p->roots = roots;
+    p->cfg = default_cfg(logN);
+    cudaGetDevice(&p->device);
+
+    const size_t table_pairs = (size_t)N * n_limbs;
+    std::vector<ulonglong2> hf(table_pairs), hi(table_pairs);
+    p->h_limbs.resize(n_limbs);
+    unsigned nthreads = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
+    nthreads = std::min<unsigned>(nthreads, n_limbs);
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nthreads; ++t) {
+        pool.emplace_back([&, t]() {
+            for (uint32_t l = t; l < n_limbs; l += nthreads)
+                fill_limb(N, logN, p->moduli[l], roots[l], &hf[(size_t)l * N], &hi[(size_t)l * N],
+                          &p->h_limbs[l]);
+        });
+    }
+    for (auto& th : pool) th.join();
+
+    const size_t tbytes = table_pairs * sizeof(ulonglong2);
+    if (cudaMalloc(&p->d_tables, 2 * tbytes) != cudaSuccess) {
+        delete p;
+        return HX_ERR_NOMEM;
+    }
+    if (cudaMalloc((void**)&p->d_limbs, n_limbs * sizeof(LimbDev)) != cudaSuccess) {
+        cudaFree(p->d_tables);
+        delete p;
+        return HX_ERR_NOMEM;
+    }
+    ulonglong2* dfwd = (ulonglong2*)p->d_tables;
+    ulonglong2* dinv = dfwd + table_pairs;
+    for (uint32_t l = 0; l < n_limbs; ++l) {
+        p->h_limbs[l].fwd = dfwd + (size_t)l * N;
+        p->h_limbs[l].inv = dinv + (size_t)l * N;
+    }
+    cudaError_t e1 = cudaMemcpy(dfwd, hf.data(), tbytes, cudaMemcpyHostToDevice);
+    cudaError_t e2 = cudaMemcpy(dinv, hi.data(), tbytes, cudaMemcpyHostToDevice);
+    cudaError_t e3 = cudaMemcpy(p->d_limbs, p->h_limbs.data(), n_limbs * sizeof(LimbDev),
+                                cudaMemcpyHostToDevice);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        cudaFree(p->d_tables);
+        cudaFree(p->d_limbs);
+        delete p;
+        return HX_ERR_CUDA;
+    }
+    p->device_bytes = 2 * tbytes + n_limbs * sizeof(LimbDev);
+    *out = p;
+    return HX_OK;
+}
+
+extern "C" int hx_plan_destroy(hx_plan_t p) {
+    if (!p) return HX_ERR_NULL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != p->device) cudaSetDevice(p->device);
+    cudaFree(p->d_tables);
+    cudaFree(p->d_limbs);
+    if (prev != p->device) cudaSetDevice(prev);
+    delete p;
+    return HX_OK;
+}
+
+extern "C" int hx_plan_roots(hx_plan_t p, uint64_t* h_roots_out) {
+    if (!p || !h_roots_out) return HX_ERR_NULL;
+    memcpy(h_roots_out, p->roots.data(), p->n_limbs * sizeof(uint64_t));
+    return HX_OK;
+}
+
+extern "C" int hx_plan_info(hx_plan_t p, uint64_t* N, uint32_t* n_limbs, uint64_t* bytes) {
+    if (!p) return HX_ERR_NULL;
+    if (N) *N = p->N;
+    if (n_limbs) *n_limbs = p->n_limbs;
+    if (bytes) *bytes = p->device_bytes;
+    return HX_OK;
+}
