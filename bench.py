@@ -1,0 +1,482 @@
+"""Throughput of the negacyclic NTT hot path on GB300, one JSON line.
+
+Workload (one step): the ciphertext-shaped product at N = 65536 with 32 RNS
+limbs of mixed 30/50/60-bit primes -- two ciphertexts of two polynomials
+each.  Forward NTT of the four input polynomials (output range [0, 4q)),
+the fused tensor product d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1 with the
+scaled accumulation r_k = d_k s + e_k (EltwiseFMAMod), inverse NTT of r_0..2:
+7 x 32 = 224 limb-transforms per step.  Inputs are seeded synthetic uniform
+residues already resident in HBM; three input sets rotate so the working set
+(3 x 112 MiB of inputs plus 112 MiB of intermediates) exceeds the 129 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hexgpu|reference]
+
+Multi-GPU (torchrun, one rank per GPU): each rank runs the same per-GPU
+workload on its own GPU (limbs and polynomials are independent; no data-path
+collective), timing is the max over ranks, value is the whole-job total.
+
+--impl reference times the CPU oracle (plain C, one thread) on a bounded
+sample of the same workload: the pipeline on three limbs (one per width).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import platform
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "NTT limb-transforms/s at N=2^16 (% of int-mul/HBM roofline); served p99 latency"
+UNIT = "limb-transforms/s"
+N_DEFAULT = 1 << 16
+LIMBS_DEFAULT = 32
+
+
+# ------------------------------------------------------------------ workload
+def workload_arrays(N, n_limbs, n_sets):
+    """n_sets input sets, each (ins, es): ins = [a0, a1, b0, b1], es = [e0, e1,
+    e2], every one a [1][n_limbs][N] uint64 array of uniform residues."""
+    wl = W.ciphertext_tensor(N=N, n_limbs=n_limbs)
+    sets = []
+    for k in range(n_sets):
+        ins = [W.poly_batch(wl.seed + 1000 * k, t, 1, wl.moduli, N) for t in range(4)]
+        es = [W.poly_batch(wl.seed + 1000 * k, 10 + t, 1, wl.moduli, N) for t in range(3)]
+        sets.append((ins, es))
+    s = W.scalars(wl.seed, 20, wl.moduli)
+    return wl, sets, s
+
+
+def device_sets(sets):
+    """Each set as two device tensors: the four inputs back to back [4][L][N]
+    and the three addends [3][L][N]."""
+    from paper_2103_16400_gb300.tensors import to_device
+    return [(to_device(np.concatenate(ins)), to_device(np.concatenate(es))) for ins, es in sets]
+
+
+#: IMAD-pipe issue slots of one exact Shoup butterfly, in units of one 32-bit
+#: mad.lo (the probes measure mad.hi and mad.wide at half that rate or less):
+#: 64-bit words -- high word of W'X from four partial products (one high
+#: half, three full products: 1*2 + 3*(1+2) = 11), remainder W X - Q q mod
+#: 2^64 from two full low products and four low halves (2*(1+2) + 4 = 10);
+#: 32-bit words -- one high half and two low halves (2 + 1 + 1 = 4).
+SLOTS_WIDE, SLOTS_NARROW = 21, 4
+
+
+def imad_slots_per_transform(N, moduli):
+    """Algorithmic IMAD-pipe slots of one limb-transform: N/2 log2 N Harvey
+    butterflies, each one Shoup product."""
+    logn = N.bit_length() - 1
+    bf = N // 2 * logn
+    return [bf * (SLOTS_NARROW if q < (1 << 30) else SLOTS_WIDE) for q in moduli]
+
+
+class HexStep:
+    """The timed step, through the C ABI, with autotuned schedules: one
+    forward call over the four inputs, the fused tensor/FMA kernel, one
+    inverse call over the three outputs.  Device buffers are preallocated."""
+
+    def __init__(self, N, moduli, s, dev_sets, torch, tune=True):
+        from paper_2103_16400_gb300 import capi, tune as hx_tune
+        from paper_2103_16400_gb300.tensors import empty
+        self.capi, self.torch = capi, torch
+        self.N, self.moduli, self.s = N, moduli, s
+        self.plan = capi.Plan(N, moduli)
+        if tune:
+            self.tuned = {"forward": hx_tune.tune(self.plan, 4, direction=capi.Plan.FORWARD),
+                          "inverse": hx_tune.tune(self.plan, 3, direction=capi.Plan.INVERSE)}
+        self.dev_sets = dev_sets
+        L = len(moduli)
+        self.A = empty((4, L, N))
+        self.R = empty((3, L, N))
+        self.stream = torch.cuda.current_stream()
+        self.fwd_events = []
+
+    def run(self, i, record=False):
+        c, N, st = self.capi, self.N, self.stream
+        ins, es = self.dev_sets[i % len(self.dev_sets)]
+        if record:
+            e0 = self.torch.cuda.Event(enable_timing=True)
+            e1 = self.torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+        c.hx_ntt_forward(self.plan, self.A, ins, 4, 1, 4, st)
+        if record:
+            e1.record(st)
+            self.fwd_events.append((e0, e1))
+        A, R = self.A, self.R
+        c.hx_dyadic_tensor_fma(R[0], R[1], R[2], A[0], A[1], A[2], A[3], self.s, es[0], es[1],
+                               es[2], N, self.moduli, 1, 4, st)
+        c.hx_ntt_inverse(self.plan, R, R, 3, 1, 1, st)
+        return [R[0:1], R[1:2], R[2:3]]
+
+
+# ------------------------------------------------------------------ clocks
+_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons during the timed region, by
+    NVML through ctypes (read-only queries), else by nvidia-smi."""
+
+    def __init__(self, device_index=0, period=0.02):
+        self.period, self.samples, self.reasons = period, [], set()
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._nvml = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                bus = os.environ.get("HX_PCI_BUS_ID")
+                ok = -1
+                if bus:
+                    ok = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h))
+                if ok != 0:
+                    ok = nv.nvmlDeviceGetHandleByIndex_v2(device_index, ctypes.byref(h))
+                if ok == 0:
+                    self._nvml, self._h = nv, h
+                    mx = ctypes.c_uint()
+                    if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                        self.max_mhz = mx.value
+        except OSError:
+            self._nvml = None
+
+    def _poll_nvml(self):
+        nv, h = self._nvml, self._h
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop.is_set():
+            if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                self.samples.append(clk.value)
+            if fn(h, ctypes.byref(rs)) == 0:
+                for bit, name in _REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            time.sleep(self.period)
+
+    def _poll_smi(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                      "-i", "0"], capture_output=True, text=True, timeout=5).stdout
+                f = [x.strip() for x in out.strip().split(",")]
+                self.samples.append(float(f[0]))
+                self.max_mhz = float(f[1])
+                for name, v in zip(names, f[2:]):
+                    if v.lower().startswith("active"):
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            time.sleep(0.2)
+
+    def __enter__(self):
+        target = self._poll_nvml if self._nvml else self._poll_smi
+        self._t = threading.Thread(target=target, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        med = float(np.median(self.samples)) if self.samples else None
+        return {"sm_mhz": med, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(N, moduli, s, sets):
+    """One bounded oracle run of the same pipeline on limbs of each width
+    (first 30-, 50- and 60-bit limb): returns (limb-transforms, seconds)."""
+    import oracle
+    pick = [0, 1, 2]
+    qs = [moduli[l] for l in pick]
+    ins, es = sets[0]
+    ins = [x[:, pick] for x in ins]
+    es = [x[:, pick] for x in es]
+    ss = np.array([s[l] for l in pick], dtype=np.uint64)
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.ciphertext_tensor(*ins, ss, *es, qs)
+    dt = time.perf_counter() - t0
+    return 7 * len(pick), dt
+
+
+def cpu_baseline(N, moduli, s, sets, min_seconds=10.0):
+    units, secs, reps = 0, 0.0, 0
+    while secs < min_seconds:
+        u, t = oracle_sample(N, moduli, s, sets)
+        units += u
+        secs += t
+        reps += 1
+    return {"value": units / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x ciphertext-tensor pipeline on 3 limbs (30/50/60-bit) at "
+                      f"N={N}: {units} limb-transforms in {secs:.2f} s, 1 thread",
+            "cpu": platform.processor() or platform.machine()}
+
+
+# ------------------------------------------------------------------ main
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    N, nl = args.N, args.limbs
+    wl, sets, s = workload_arrays(N, nl, 1)
+    for _ in range(args.warmup):
+        oracle_sample(N, wl.moduli, s, sets)
+    units, secs = 0, 0.0
+    for _ in range(args.steps):
+        u, t = oracle_sample(N, wl.moduli, s, sets)
+        units += u
+        secs += t
+    value = units / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"ciphertext_tensor_n{N}_l{nl} (oracle sample: 3 limbs)",
+                       "N": N, "limbs": nl},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step: pipeline on 3 limbs (30/50/60-bit), "
+                                       f"21 limb-transforms, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_case(args):
+    """One kernel family alone, for profiling and tuning (not the contract line)."""
+    import torch
+    from paper_2103_16400_gb300 import build as hbuild, capi
+    from paper_2103_16400_gb300.tensors import empty, to_device
+    hbuild.build()
+    N, nl = args.N, args.limbs
+    out = {"case": args.case, "N": N, "limbs": nl}
+    if args.case == "probes":
+        for kind in capi.PROBE_KINDS:
+            r, ms = capi.hx_probe_int_mul_rate(kind, 8192)
+            out[f"int_mul_{kind}_Tops"] = r / 1e12
+        for w in W.WIDTHS:
+            q = W.ntt_primes(w, W.MIXED_TWO_N, 1)[0]
+            for v in (0, 1, 2):
+                for inv in (False, True):
+                    if w == 30 and v > 0:
+                        continue
+                    r, ms = capi.hx_probe_butterfly_rate(q, v, inv, 8192)
+                    out[f"bfly_{w}bit_v{v}_{'inv' if inv else 'fwd'}_T_per_s"] = r / 1e12
+        print(json.dumps(out))
+        return 0
+    wl = W.ciphertext_tensor(N=N, n_limbs=nl)
+    P = args.polys
+    n_sets = 2
+    xs = [to_device(W.poly_batch(wl.seed + k, 0, P, wl.moduli, N)) for k in range(n_sets)]
+    ys = [empty(x.shape) for x in xs]
+    plan = capi.Plan(N, wl.moduli)
+    s = W.scalars(wl.seed, 20, wl.moduli)
+    st = torch.cuda.current_stream()
+
+    def once(i):
+        x, y = xs[i % n_sets], ys[i % n_sets]
+        if args.case == "fwd":
+            capi.hx_ntt_forward(plan, y, x, P, 1, 4, st)
+        elif args.case == "inv":
+            capi.hx_ntt_inverse(plan, y, x, P, 1, 1, st)
+        else:
+            # P/4 ciphertext pairs: A0..B1 are the four quarters of x, the
+            # addends the first three quarters of the other set, outputs in y
+            Q, o = P // 4, xs[(i + 1) % n_sets]
+            capi.hx_dyadic_tensor_fma(y[:Q], y[Q:2 * Q], y[2 * Q:3 * Q], x[:Q], x[Q:2 * Q],
+                                      x[2 * Q:3 * Q], x[3 * Q:], s, o[:Q], o[Q:2 * Q],
+                                      o[2 * Q:3 * Q], N, wl.moduli, Q, 4, st)
+
+    for i in range(max(args.warmup, 1)):
+        once(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(args.steps):
+        once(i)
+    e1.record(st)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / args.steps
+    out.update({"polys": P, "us_per_call": us})
+    if args.case in ("fwd", "inv"):
+        out["limb_transforms_per_s"] = P * nl / (us * 1e-6)
+        ops = sum(imad_slots_per_transform(N, wl.moduli)) * P
+        out["imad_slot_T_per_s"] = ops / (us * 1e-6) / 1e12
+        out["hbm_alg_GBs"] = 16 * N * nl * P / (us * 1e-6) / 1e9
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hexgpu", choices=["hexgpu", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--limbs", type=int, default=LIMBS_DEFAULT)
+    ap.add_argument("--sets", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--case", default="pipeline",
+                    choices=["pipeline", "fwd", "inv", "tensor", "probes"],
+                    help="pipeline: the contract line; others: one kernel family alone "
+                         "(diagnostic line, used for profiling)")
+    ap.add_argument("--polys", type=int, default=8, help="polynomials per call for --case fwd/inv")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.case != "pipeline":
+        return run_case(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2103_16400_gb300 import build as hbuild, capi
+    from paper_2103_16400_gb300.tensors import pinned_from
+    hbuild.build()
+
+    N, nl = args.N, args.limbs
+    wl, sets, s = workload_arrays(N, nl, args.sets)
+    dev_sets = device_sets(sets)
+    step = HexStep(N, wl.moduli, s, dev_sets, torch)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        step.run(i)
+    barrier()
+    stream = step.stream
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    launches0 = capi.hx_launch_count()
+    with ClockSampler(local) as clocks:
+        t0.record(stream)
+        for i in range(args.steps):
+            step.run(i, record=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = capi.hx_launch_count() - launches0
+    total_ms = t0.elapsed_time(t1)
+    fwd_ms = [a.elapsed_time(b) for a, b in step.fwd_events]
+    if ws > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    barrier()
+
+    per_step_units = 7 * nl
+    value = per_step_units * args.steps * ws / (total_ms / 1e3)
+
+    # roofline of the dominant kernel: the forward NTT call (4 polynomials,
+    # two pass launches), IMAD-bound; peak = mad.lo issue rate probed live
+    imad_rate, _ = capi.hx_probe_int_mul_rate("mad.lo", 8192)
+    fwd_call_ms = float(np.mean(fwd_ms))
+    alg_slots = 4 * sum(imad_slots_per_transform(N, wl.moduli))
+    achieved = alg_slots / (fwd_call_ms * 1e-3)
+    fwd_bytes = 4 * 16 * N * nl
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": imad_rate / 1e12,
+                "unit": "T IMAD-slot/s", "frac": achieved / imad_rate, "traffic": None,
+                "kernel": "hx_ntt_forward, 4 polys x 32 limbs (ntt pass kernels, 2 launches)",
+                "fwd_call_us": fwd_call_ms * 1e3,
+                "alg_slots_per_call": alg_slots,
+                "hbm_gbs_algorithmic": fwd_bytes / (fwd_call_ms * 1e-3) / 1e9,
+                "peak_source": "hx_probe_int_mul_rate mad.lo.u32 (1 slot), measured live",
+                "schedules": {k: v.get("forward" if k == "forward" else "inverse")
+                              for k, v in getattr(step, "tuned", {}).items()}}
+
+    # end to end through the public API with host buffers
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 50))
+    host_in = [(pinned_from(np.concatenate(ins)), pinned_from(np.concatenate(es)))
+               for ins, es in sets]
+    host_out = torch.empty((3, nl, N), dtype=torch.int64).pin_memory()
+    h2d = sum(x.numel() * 8 for x in host_in[0])
+    d2h = host_out.numel() * 8
+
+    def e2e_step(i):
+        hi, he = host_in[i % len(host_in)]
+        di, de = dev_sets[i % len(dev_sets)]
+        di.copy_(hi, non_blocking=True)
+        de.copy_(he, non_blocking=True)
+        step.run(i)
+        host_out.copy_(step.R, non_blocking=True)
+
+    for i in range(3):
+        e2e_step(i)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = per_step_units * e2e_steps * ws / (e2e_ms / 1e3)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"ciphertext_tensor_n{N}_l{nl}", "N": N, "limbs": nl,
+                       "widths": "30/50/60-bit, limb l -> (30,50,60)[l%3]",
+                       "polys_per_step": "4 in (fwd), 3 out (inv)",
+                       "limb_transforms_per_step": per_step_units,
+                       "l2": f"{args.sets} rotating input sets, "
+                             f"{args.sets * 7 * nl * N * 8 / 2**20:.0f} MiB of inputs > 129 MB L2",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clocks.summary()}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(N, wl.moduli, s, sets)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -104,6 +104,24 @@ int hx_plan_roots(hx_plan_t plan, uint64_t* h_roots_out);
 /* Plan shape: N, limb count and the device bytes the plan holds. */
 int hx_plan_info(hx_plan_t plan, uint64_t* N, uint32_t* n_limbs, uint64_t* device_bytes);
 
+/* Kernel schedule of the plan's transforms -- the knob the autotuner turns;
+ * any valid schedule gives identical results, only speed differs (the paper
+ * suggests choosing implementations by trials, Section 3.2).  npass is 1 or
+ * 2; params holds six int32 per pass, in stage order:
+ *   {s0, K, logGb, logGc, logR, pipe}
+ * pass covers stages [s0, s0 + K) of the log2 N stages; a tile is
+ * 2^logGb x 2^K x 2^logGc elements (top-index values x stage bits x
+ * low-index values); 2^logR elements per thread; pipe = 1 selects the
+ * persistent double-buffered kernel.  hx_plan_set_schedule returns
+ * HX_ERR_ARG for a schedule the library cannot run (stages not covering
+ * [0, log2 N), unsupported K or logR, tile too large).  `direction` selects
+ * the forward (1) or inverse (2) transform's schedule, or both (3, set
+ * only); the inverse runs the same passes in reverse order.
+ * hx_plan_get_schedule writes 12 int32 (the unused second pass zeroed). */
+int hx_plan_set_schedule(hx_plan_t plan, uint32_t direction, uint32_t npass,
+                         const int32_t* params);
+int hx_plan_get_schedule(hx_plan_t plan, uint32_t direction, uint32_t* npass, int32_t* params);
+
 /* ----------------------------------------------------------------- transforms
  * hx_ntt_forward: forward negacyclic NTT of every limb of n_polys
  *   polynomials (Section 2.2, Algorithm "Cooley-Tukey Radix-2 NTT" with the
@@ -207,6 +225,32 @@ int hx_dyadic_tensor_fma(uint64_t* d_r0, uint64_t* d_r1, uint64_t* d_r2, const u
                          const uint64_t* d_e2, uint64_t n, const uint64_t* h_moduli,
                          uint32_t n_limbs, uint32_t n_polys, uint32_t input_mod_factor,
                          hx_stream_t stream);
+
+/* ---------------------------------------------------------------- measurement
+ * Support for the benchmark; the paper has no counterpart.
+ *
+ * hx_launch_count: number of CUDA kernels this library has launched in this
+ *   process (all entry points, all devices), for launch accounting.
+ * hx_probe_int_mul_rate: runs a grid of 8 blocks of 256 threads per SM in
+ *   which every thread executes `iters` x 16 instructions of one 32-bit
+ *   integer multiply form in 8 independent dependency chains -- kind 0:
+ *   mad.lo.u32, kind 1: mad.hi.u32, kind 2: mad.wide.u32, kind 3: lo and hi
+ *   alternating -- and returns the achieved rate in *ops_per_s (and the
+ *   kernel time in *ms if not NULL): the integer-multiply roofline of this
+ *   GPU at its current clocks.  Synchronises `stream`.
+ * hx_probe_butterfly_rate: the same grid running Harvey butterflies for
+ *   modulus q on register-resident data (4 per thread per iteration);
+ *   `variant` bits 0-3 pick the 64-bit Shoup-product code (0: compiler's
+ *   64-bit products, 1: mad.wide high word, 2: carry-chain high word), bit 4
+ *   the inverse butterfly.  Returns butterflies per second.  Synchronises
+ *   `stream`.
+ * Errors: HX_ERR_NULL, HX_ERR_ARG, HX_ERR_NOMEM, HX_ERR_CUDA.
+ */
+uint64_t hx_launch_count(void);
+int hx_probe_int_mul_rate(uint32_t kind, uint32_t iters, double* ops_per_s, float* ms,
+                          hx_stream_t stream);
+int hx_probe_butterfly_rate(uint32_t variant, uint32_t iters, uint64_t q,
+                            double* butterflies_per_s, float* ms, hx_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,8 @@ _SIGS = {
     "hx_plan_destroy": [VP],
     "hx_plan_roots": [VP, P64],
     "hx_plan_info": [VP, P64, ctypes.POINTER(U32), P64],
+    "hx_plan_set_schedule": [VP, U32, U32, ctypes.POINTER(ctypes.c_int32)],
+    "hx_plan_get_schedule": [VP, U32, ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_int32)],
     "hx_ntt_forward": [VP, VP, VP, U32, U32, U32, VP],
     "hx_ntt_inverse": [VP, VP, VP, U32, U32, U32, VP],
     "hx_ntt_forward_raw": [VP, U64, P64, U32, U32, U32, VP],
@@ -40,8 +42,13 @@ _SIGS = {
     "hx_ciphertext_tensor": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, VP],
     "hx_dyadic_tensor_fma": [VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U64, P64, U32, U32,
                              U32, VP],
+    "hx_launch_count": [],
+    "hx_probe_int_mul_rate": [U32, U32, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_float), VP],
+    "hx_probe_butterfly_rate": [U32, U32, U64, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_float), VP],
 }
-_RESTYPES = {"hx_strerror": ctypes.c_char_p}
+_RESTYPES = {"hx_strerror": ctypes.c_char_p, "hx_launch_count": U64}
 
 _lib = None
 _lock = threading.Lock()
@@ -130,6 +137,22 @@ class Plan:
                                                    ctypes.byref(nl), ctypes.byref(b)))
         return N.value, nl.value, b.value
 
+    FORWARD, INVERSE, BOTH = 1, 2, 3
+
+    def schedule(self, direction: int = 1):
+        """Kernel schedule of the forward (1) or inverse (2) transform: a list
+        of (s0, K, logGb, logGc, logR, pipe) per pass."""
+        n, p = U32(), (ctypes.c_int32 * 12)()
+        _check("hx_plan_get_schedule",
+               load().hx_plan_get_schedule(self.handle, direction, ctypes.byref(n), p))
+        return [tuple(p[6 * i:6 * i + 6]) for i in range(n.value)]
+
+    def set_schedule(self, passes, direction: int = 3):
+        flat = [int(v) for ps in passes for v in ps]
+        arr = (ctypes.c_int32 * len(flat))(*flat)
+        _check("hx_plan_set_schedule",
+               load().hx_plan_set_schedule(self.handle, direction, len(passes), arr))
+
     def destroy(self):
         if getattr(self, "handle", None):
             _check("hx_plan_destroy", load().hx_plan_destroy(self.handle))
@@ -217,3 +240,30 @@ def hx_dyadic_tensor_fma(r0, r1, r2, A0, A1, B0, B1, scalars, e0, e1, e2, n: int
         ptr(r0), ptr(r1), ptr(r2), ptr(A0), ptr(A1), ptr(B0), ptr(B1), host_u64(scalars),
         ptr(e0), ptr(e1), ptr(e2), n, host_u64(moduli), len(moduli), n_polys,
         input_mod_factor, _stream(stream)))
+
+
+def hx_launch_count() -> int:
+    return int(load().hx_launch_count())
+
+
+PROBE_KINDS = {"mad.lo": 0, "mad.hi": 1, "mad.wide": 2, "lo+hi": 3}
+
+
+def hx_probe_int_mul_rate(kind="mad.lo", iters: int = 4096, stream=None):
+    """(32-bit integer multiply instructions per second, kernel ms) of one
+    multiply form on the current GPU."""
+    r, t = ctypes.c_double(), ctypes.c_float()
+    _check("hx_probe_int_mul_rate", load().hx_probe_int_mul_rate(
+        PROBE_KINDS.get(kind, kind), iters, ctypes.byref(r), ctypes.byref(t), _stream(stream)))
+    return r.value, t.value
+
+
+def hx_probe_butterfly_rate(q: int, variant: int = 1, inverse: bool = False, iters: int = 4096,
+                            stream=None):
+    """(Harvey butterflies per second, kernel ms) for modulus q and one
+    Shoup-product variant."""
+    r, t = ctypes.c_double(), ctypes.c_float()
+    _check("hx_probe_butterfly_rate", load().hx_probe_butterfly_rate(
+        variant | (16 if inverse else 0), iters, q, ctypes.byref(r), ctypes.byref(t),
+        _stream(stream)))
+    return r.value, t.value

@@ -116,7 +116,7 @@ int hx_ntt_forward(hx_plan_t plan, uint64_t* r, const uint64_t* x, uint32_t n_po
                    uint32_t in_mf, uint32_t out_mf, hx_stream_t stream) {
     int st = check_ntt(plan, r, x, n_polys, in_mf, out_mf, true);
     if (st != HX_OK) return st;
-    return cuda_status(launch_ntt(plan, r, x, n_polys, true, in_mf, out_mf, plan->cfg,
+    return cuda_status(launch_ntt(plan, r, x, n_polys, true, in_mf, out_mf, plan->cfg_fwd,
                                   (cudaStream_t)stream));
 }
 
@@ -124,7 +124,7 @@ int hx_ntt_inverse(hx_plan_t plan, uint64_t* r, const uint64_t* x, uint32_t n_po
                    uint32_t in_mf, uint32_t out_mf, hx_stream_t stream) {
     int st = check_ntt(plan, r, x, n_polys, in_mf, out_mf, false);
     if (st != HX_OK) return st;
-    return cuda_status(launch_ntt(plan, r, x, n_polys, false, in_mf, out_mf, plan->cfg,
+    return cuda_status(launch_ntt(plan, r, x, n_polys, false, in_mf, out_mf, plan->cfg_inv,
                                   (cudaStream_t)stream));
 }
 
@@ -259,15 +259,26 @@ int hx_ciphertext_tensor(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* o
     for (uint32_t l = 0; l < plan->n_limbs; ++l)
         if (plan->moduli[l] >= (1ull << 61)) return HX_ERR_MODULUS;
     int st;
+    // operands laid out back to back ([4][n_polys][limbs][N], [3][...]) are
+    // transformed by one call each, which fills the GPU better than four/three
+    const uint64_t S = (uint64_t)n_polys * plan->n_limbs * plan->N;
     uint64_t* ins[4] = {a0, a1, b0, b1};
-    for (auto x : ins)
-        if ((st = hx_ntt_forward(plan, x, x, n_polys, 1, 4, stream)) != HX_OK) return st;
+    if (a1 == a0 + S && b0 == a0 + 2 * S && b1 == a0 + 3 * S && (uint64_t)n_polys * 4 < (1u << 31)) {
+        if ((st = hx_ntt_forward(plan, a0, a0, 4 * n_polys, 1, 4, stream)) != HX_OK) return st;
+    } else {
+        for (auto x : ins)
+            if ((st = hx_ntt_forward(plan, x, x, n_polys, 1, 4, stream)) != HX_OK) return st;
+    }
     st = hx_dyadic_tensor_fma(o0, o1, o2, a0, a1, b0, b1, h_scalars, e0, e1, e2, plan->N,
                               plan->moduli.data(), plan->n_limbs, n_polys, 4, stream);
     if (st != HX_OK) return st;
     uint64_t* outs[3] = {o0, o1, o2};
-    for (auto x : outs)
-        if ((st = hx_ntt_inverse(plan, x, x, n_polys, 1, 1, stream)) != HX_OK) return st;
+    if (o1 == o0 + S && o2 == o0 + 2 * S) {
+        if ((st = hx_ntt_inverse(plan, o0, o0, 3 * n_polys, 1, 1, stream)) != HX_OK) return st;
+    } else {
+        for (auto x : outs)
+            if ((st = hx_ntt_inverse(plan, x, x, n_polys, 1, 1, stream)) != HX_OK) return st;
+    }
     return HX_OK;
 }
 

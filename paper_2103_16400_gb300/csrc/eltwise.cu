@@ -183,6 +183,7 @@ static cudaError_t launch_one(uint64_t* r, const uint64_t* a, const uint64_t* b,
         dim3 grid = elt_grid(g.n, rows, 256, (g.n & 1) == 0);
         eltwise_kernel<OP, INMF, ADDEND><<<grid, 256, 0, st>>>(
             r + poly_off, a + poly_off, b ? b + poly_off : nullptr, c, gg);
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -259,6 +260,7 @@ cudaError_t launch_tensor_fma(uint64_t* r0, uint64_t* r1, uint64_t* r2, const ui
                     break;
                 default: return cudaErrorInvalidValue;
             }
+            count_launch();
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }

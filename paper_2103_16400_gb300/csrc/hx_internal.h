@@ -23,9 +23,11 @@ struct LimbDev {
 };
 
 // One pass of a transform: CT stages [s0, s0 + K) on tiles of
-// 2^logGb (top-index values) x 2^K x 2^logGc (low-index values) elements.
+// 2^logGb (top-index values) x 2^K x 2^logGc (low-index values) elements,
+// 2^logR elements per thread; pipe selects the persistent double-buffered
+// kernel (1) or one block per tile (0).
 struct PassCfg {
-    int s0, K, logGb, logGc, logR;
+    int s0, K, logGb, logGc, logR, pipe;
 };
 
 struct NttCfg {
@@ -45,16 +47,19 @@ struct hx_plan_s {
     hx::LimbDev* d_limbs = nullptr;
     std::vector<hx::LimbDev> h_limbs;
     uint64_t device_bytes = 0;
-    hx::NttCfg cfg{};
+    hx::NttCfg cfg_fwd{}, cfg_inv{};   // kernel schedules per direction
 };
 
 namespace hx {
+
+// probe.cu: counts kernel launches made by this library (all entry points)
+void count_launch(uint64_t n = 1);
 
 // plan.cpp
 bool is_prime_u64(uint64_t n);
 uint64_t powmod_u64(uint64_t a, uint64_t e, uint64_t q);
 uint64_t min_primitive_root(uint64_t N, uint64_t q);
-NttCfg default_cfg(int logN);
+NttCfg default_cfg(int logN, bool forward);
 
 // ntt.cu
 cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,

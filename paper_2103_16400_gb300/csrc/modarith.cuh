@@ -27,22 +27,111 @@ __device__ __forceinline__ uint64_t shoup_mul_lazy64(uint64_t x, uint64_t w, uin
     return w * x - Q * q;
 }
 
+// The same product built explicitly from 32-bit multiplies, keeping carries
+// and the final subtraction on the integer-multiply pipe rather than the ALU:
+//
+//   high word of a*b, a = a1:a0, b = b1:b0 (32-bit halves):
+//     u = a0 b1 + hi(a0 b0)         < 2^64, no carry out
+//     v = a1 b0 + lo32(u)           < 2^64
+//     r = a1 b1 + hi32(u) + hi32(v)
+//   (mul.hi + three mad.wide + one 64-bit add), or as a mad.lo.cc/madc.hi
+//   carry chain over the same four partial products;
+//
+//   T = W X - Q q mod 2^64 = W X + Q (2^64 - q) mod 2^64: only the low word is
+//   needed, so T = w0 x0 + Q0 n0 (two wide products summed mod 2^64) plus
+//   2^32 (w0 x1 + w1 x0 + Q0 n1 + Q1 n0) mod 2^64 (four low-half mads).
+__device__ __forceinline__ uint64_t mulhi64_wide(uint64_t a, uint64_t b) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint32_t h;
+    uint64_t u, v, r;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(h) : "r"(a0), "r"(b0));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(u) : "r"(a0), "r"(b1), "l"((uint64_t)h));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(v) : "r"(a1), "r"(b0), "l"(u & 0xffffffffull));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a1), "r"(b1), "l"(u >> 32));
+    return r + (v >> 32);
+}
+
+__device__ __forceinline__ uint64_t mulhi64_cc(uint64_t a, uint64_t b) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint32_t r0, r1;
+    asm("{\n\t.reg .u32 h, m;\n\t"
+        "mul.hi.u32 h, %2, %4;\n\t"
+        "mad.lo.cc.u32 h, %2, %5, h;\n\t"
+        "madc.hi.u32 m, %2, %5, 0;\n\t"
+        "mad.lo.cc.u32 h, %3, %4, h;\n\t"
+        "madc.hi.cc.u32 m, %3, %4, m;\n\t"
+        "madc.hi.u32 %1, %3, %5, 0;\n\t"
+        "mad.lo.cc.u32 %0, %3, %5, m;\n\t"
+        "addc.u32 %1, %1, 0;\n\t}"
+        : "=r"(r0), "=r"(r1)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    return ((uint64_t)r1 << 32) | r0;
+}
+
+// (w x + Q nq) mod 2^64 with nq = 2^64 - q: the Shoup remainder W X - Q q.
+__device__ __forceinline__ uint64_t shoup_rem64(uint64_t w, uint64_t x, uint64_t Q,
+                                                uint64_t nq) {
+    const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32);
+    const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+    const uint32_t Q0 = (uint32_t)Q, Q1 = (uint32_t)(Q >> 32);
+    const uint32_t n0 = (uint32_t)nq, n1 = (uint32_t)(nq >> 32);
+    uint64_t t;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(t) : "r"(w0), "r"(x0));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(t) : "r"(Q0), "r"(n0));
+    uint32_t th = (uint32_t)(t >> 32);
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(th) : "r"(w0), "r"(x1));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(th) : "r"(w1), "r"(x0));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(th) : "r"(Q0), "r"(n1));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(th) : "r"(Q1), "r"(n0));
+    return ((uint64_t)th << 32) | (uint32_t)t;
+}
+
+// Shoup product variants (V): 0 plain C++; 1 mad.wide high word + explicit
+// remainder; 2 carry-chain high word + explicit remainder.  All return the
+// same value, w x mod q in [0, 2q).
+template <int V>
+__device__ __forceinline__ uint64_t shoup_lazy64v(uint64_t x, uint64_t w, uint64_t wp, uint64_t q,
+                                                  uint64_t nq) {
+    if constexpr (V == 0) {
+        return shoup_mul_lazy64(x, w, wp, q);
+    } else {
+        const uint64_t Q = V == 1 ? mulhi64_wide(wp, x) : mulhi64_cc(wp, x);
+        return shoup_rem64(w, x, Q, nq);
+    }
+}
+
+#ifndef HX_SHOUP_VARIANT
+#define HX_SHOUP_VARIANT 2
+#endif
+
+// x in [0, 4q) -> [0, 2q): subtract 2q unless that borrows.  Since 2q < 2^63
+// and x < 2^64, x - 2q wraps past 2^63 exactly when x < 2q, so the sign bit
+// of the difference decides.
+__device__ __forceinline__ uint64_t reduce_2q(uint64_t x, uint64_t two_q) {
+    const uint64_t d = x - two_q;
+    return (int64_t)d < 0 ? x : d;
+}
+
 // Harvey forward butterfly: X0, X1 in [0, 4q) -> X0 + W X1, X0 - W X1 in [0, 4q).
+template <int V = HX_SHOUP_VARIANT>
 __device__ __forceinline__ void harvey_fwd64(uint64_t& X0, uint64_t& X1, uint64_t W,
                                              uint64_t Wp, uint64_t q, uint64_t two_q) {
-    uint64_t x0 = X0 >= two_q ? X0 - two_q : X0;
-    uint64_t T = shoup_mul_lazy64(X1, W, Wp, q);
+    const uint64_t x0 = V == 0 ? (X0 >= two_q ? X0 - two_q : X0) : reduce_2q(X0, two_q);
+    const uint64_t T = shoup_lazy64v<V>(X1, W, Wp, q, 0 - q);
     X0 = x0 + T;
     X1 = x0 - T + two_q;
 }
 
 // Harvey inverse butterfly: X0, X1 in [0, 2q) -> X0 + X1, W (X0 - X1) in [0, 2q).
+template <int V = HX_SHOUP_VARIANT>
 __device__ __forceinline__ void harvey_inv64(uint64_t& X0, uint64_t& X1, uint64_t W,
                                              uint64_t Wp, uint64_t q, uint64_t two_q) {
     uint64_t y0 = X0 + X1;
-    y0 = y0 >= two_q ? y0 - two_q : y0;
-    uint64_t T = X0 - X1 + two_q;
-    X1 = shoup_mul_lazy64(T, W, Wp, q);
+    y0 = V == 0 ? (y0 >= two_q ? y0 - two_q : y0) : reduce_2q(y0, two_q);
+    const uint64_t T = X0 - X1 + two_q;
+    X1 = shoup_lazy64v<V>(T, W, Wp, q, 0 - q);
     X0 = y0;
 }
 

@@ -1,0 +1,563 @@
+// Fused negacyclic NTT pass kernels for sm_103a (templates; instantiated in
+// ntt_fwd.cu and ntt_inv.cu).
+//
+// The forward transform is the radix-2 Cooley-Tukey NTT of Section 2.2 with
+// the Harvey butterfly (values kept lazily in [0, 4q)); the inverse is the
+// radix-2 Gentleman-Sande InvNTT with the Harvey inverse butterfly (values in
+// [0, 2q)) and the N^-1 scaling folded into its last stage.  Both index the
+// twiddles as the paper's algorithms do: stage s (s = 0 .. log2 N - 1,
+// m = 2^s) pairs element j with j + N/2^(s+1) and uses table entry
+// 2^s + (j >> (log2 N - s)) -- psi_rev for the forward, psi^-1_rev for the
+// inverse, whose loop runs the same stages in reverse order.
+//
+// GPU design (not the paper's AVX512 one): a pass takes K consecutive stages
+// for a tile of 2^logGb x 2^K x 2^logGc elements that those stages keep
+// closed (fixed top index bits b, fixed low index bits c).  Within the tile
+// the K stages run as register rounds: each thread holds 2^LOG_R elements and
+// applies up to LOG_R stages to them entirely in registers; consecutive
+// rounds exchange through an XOR-swizzled shared-memory tile.  The first
+// round reads its registers straight from HBM and the last round writes
+// straight back whenever the round's element-to-thread map is coalesced
+// (column passes, and the low-stage end of row passes); otherwise the tile is
+// staged through shared memory with 16-byte vector copies.  Twiddle pairs
+// {W, W'} are read through the read-only path from one base pointer per
+// (round, sub-stage, group) plus compile-time offsets.
+#pragma once
+#include <stdint.h>
+
+#include "hx_internal.h"
+#include "modarith.cuh"
+
+namespace hx {
+
+struct PassArgs {
+    uint64_t* out;
+    const uint64_t* in;
+    const LimbDev* limbs;
+    uint32_t n_limbs;
+    uint32_t n_polys;
+    int L;            // log2 N
+    int s0;           // first stage of the pass
+    int logGb;        // log2 of top-index values per tile
+    int logGc;        // log2 of low-index values per tile (0 when the pass ends at stage L-1)
+    int log_tiles_c;  // log2 of tiles along the low index
+    uint32_t last;    // this pass finishes the transform
+    uint32_t out_mf;  // output mod factor (applied when last)
+};
+
+// K stages split into ceil(K / LOG_R) rounds of near-equal size; round i
+// covers e-bits [off(i), off(i) + size(i)) counted from the top (the pass's
+// first stage acts on the top e-bit).
+template <int K, int LOG_R>
+struct Sched {
+    static constexpr int NR = (K + LOG_R - 1) / LOG_R;
+    __host__ __device__ static constexpr int size(int i) { return K / NR + (i < K % NR ? 1 : 0); }
+    __host__ __device__ static constexpr int off(int i) {
+        int s = 0;
+        for (int j = 0; j < i; ++j) s += size(j);
+        return s;
+    }
+};
+
+// Shared-memory position of local element l: XOR bits 0..3 with bits 4..7 so
+// that column-wise and stride-2^r row-wise half-warp accesses hit distinct
+// 8-byte bank pairs.
+__device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 4) & 15u); }
+
+template <typename Wd>
+struct Word;
+
+template <>
+struct Word<uint64_t> {
+    static __device__ __forceinline__ void fwd(uint64_t& a, uint64_t& b, ulonglong2 w, uint64_t q,
+                                               uint64_t q2) {
+        harvey_fwd64(a, b, w.x, w.y, q, q2);
+    }
+    static __device__ __forceinline__ void inv(uint64_t& a, uint64_t& b, ulonglong2 w, uint64_t q,
+                                               uint64_t q2) {
+        harvey_inv64(a, b, w.x, w.y, q, q2);
+    }
+    static __device__ __forceinline__ uint64_t mul(uint64_t x, uint64_t w, uint64_t wp,
+                                                   uint64_t q) {
+        return shoup_lazy64v<HX_SHOUP_VARIANT>(x, w, wp, q, 0 - q);
+    }
+};
+
+template <>
+struct Word<uint32_t> {
+    static __device__ __forceinline__ void fwd(uint32_t& a, uint32_t& b, ulonglong2 w, uint64_t q,
+                                               uint64_t q2) {
+        harvey_fwd32(a, b, (uint32_t)w.x, (uint32_t)w.y, (uint32_t)q, (uint32_t)q2);
+    }
+    static __device__ __forceinline__ void inv(uint32_t& a, uint32_t& b, ulonglong2 w, uint64_t q,
+                                               uint64_t q2) {
+        harvey_inv32(a, b, (uint32_t)w.x, (uint32_t)w.y, (uint32_t)q, (uint32_t)q2);
+    }
+    static __device__ __forceinline__ uint32_t mul(uint32_t x, uint64_t w, uint64_t wp,
+                                                   uint64_t q) {
+        return shoup_mul_lazy32(x, (uint32_t)w, (uint32_t)wp, (uint32_t)q);
+    }
+};
+
+struct TileCtx {
+    const uint64_t* gin;   // this transform's input, element 0
+    uint64_t* gout;        // this transform's output, element 0
+    uint64_t b_base;       // first top-index value of the tile
+    uint64_t c_base;       // first low-index value of the tile
+    int L, s0, logGc, w;   // w = L - s0 - K: low bits below the pass's stages
+    uint32_t nthreads;
+    uint32_t out_mf;
+    bool last;
+};
+
+// Global index of local tile element l = (bl, e, cl).
+template <int K>
+__device__ __forceinline__ uint64_t tile_gidx(uint32_t l, const TileCtx& t) {
+    if (t.w == 0) return (t.b_base << K) + l;
+    const uint32_t cl = l & ((1u << t.logGc) - 1);
+    const uint32_t rho = l >> t.logGc;
+    const uint64_t e = rho & ((1u << K) - 1);
+    const uint64_t bl = rho >> K;
+    return ((t.b_base + bl) << (t.L - t.s0)) + (e << t.w) + t.c_base + cl;
+}
+
+enum { IO_SMEM = 0, IO_GLOBAL = 1 };
+
+// One register round: stages s0+P .. s0+P+R-1 of the pass.  Each thread holds
+// 2^LOG_R elements = U = 2^(LOG_R-R) independent groups of 2^R; register index
+// reg = (v << (LOG_R - R)) | u, so the butterfly pair of sub-stage k differs
+// in register bit LOG_R-1-k (a compile-time position).  Group g = u * T + tid
+// (T threads) has bits [bl | e_hi (P) | e_lo (K-P-R) | cl (logGc)].
+template <bool FWD, typename Wd, int LOG_R, int K, int P, int R, int SRC, int DST>
+__device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __restrict__ tw,
+                                          const LimbDev& lc, const TileCtx& c) {
+    constexpr int RN = 1 << LOG_R;
+    constexpr int U = 1 << (LOG_R - R);
+    constexpr int ELO = K - P - R;
+    Wd x[RN];
+    uint64_t pfx[U];
+    uint32_t lbase[U];
+    const uint32_t cmask = (1u << c.logGc) - 1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t g = u * c.nthreads + threadIdx.x;
+        const uint32_t cl = g & cmask;
+        const uint32_t t1 = g >> c.logGc;
+        const uint32_t elo = t1 & ((1u << ELO) - 1);
+        const uint32_t t2 = t1 >> ELO;
+        const uint32_t ehi = t2 & ((1u << P) - 1);
+        const uint32_t bl = t2 >> P;
+        lbase[u] = (bl << (K + c.logGc)) | (ehi << (K - P + c.logGc)) | (elo << c.logGc) | cl;
+        pfx[u] = ((c.b_base + bl) << P) | ehi;
+    }
+    const int sshift = ELO + c.logGc;   // v stride in the tile
+    const int gshift = ELO + c.w;       // v stride in global memory
+
+    if (SRC == IO_GLOBAL) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t* p = c.gin + tile_gidx<K>(lbase[u], c);
+#pragma unroll
+            for (int v = 0; v < (1 << R); ++v)
+                x[(v << (LOG_R - R)) | u] = (Wd)__ldg(p + ((uint64_t)v << gshift));
+        }
+    } else {
+#pragma unroll
+        for (int reg = 0; reg < RN; ++reg) {
+            const int u = reg & (U - 1), v = reg >> (LOG_R - R);
+            x[reg] = (Wd)sm[swz(lbase[u] + ((uint32_t)v << sshift))];
+        }
+    }
+
+    const uint64_t q = lc.q, q2 = lc.two_q;
+#pragma unroll
+    for (int kk = 0; kk < R; ++kk) {
+        const int k = FWD ? kk : R - 1 - kk;
+        const int s = c.s0 + P + k;
+        const int hb = LOG_R - 1 - k;
+        if (!FWD && P == 0 && k == 0 && c.s0 == 0) {
+            // stage 0 of the inverse: N^-1 folded into the last butterfly
+#pragma unroll
+            for (int reg0 = 0; reg0 < RN; ++reg0) {
+                if (reg0 & (1 << hb)) continue;
+                const int reg1 = reg0 | (1 << hb);
+                const Wd a = x[reg0], b = x[reg1];
+                const Wd sum = a + b;              // [0, 4q)
+                const Wd dif = a - b + (Wd)q2;     // (0, 4q)
+                x[reg0] = Word<Wd>::mul(sum, lc.ninv, lc.ninv_p, q);
+                x[reg1] = Word<Wd>::mul(dif, lc.ninv_w, lc.ninv_w_p, q);
+            }
+            continue;
+        }
+        const ulonglong2* tb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) tb[u] = tw + ((1ull << s) + (pfx[u] << k));
+#pragma unroll
+        for (int reg0 = 0; reg0 < RN; ++reg0) {
+            if (reg0 & (1 << hb)) continue;
+            const int reg1 = reg0 | (1 << hb);
+            const int u = reg0 & (U - 1), v0 = reg0 >> (LOG_R - R);
+            const ulonglong2 w = __ldg(tb[u] + (v0 >> (R - k)));
+            if (FWD)
+                Word<Wd>::fwd(x[reg0], x[reg1], w, q, q2);
+            else
+                Word<Wd>::inv(x[reg0], x[reg1], w, q, q2);
+        }
+    }
+    if (c.last && c.out_mf == 1) {
+#pragma unroll
+        for (int reg = 0; reg < RN; ++reg) {
+            Wd y = x[reg];
+            if (FWD) y = y >= (Wd)q2 ? y - (Wd)q2 : y;
+            x[reg] = y >= (Wd)q ? y - (Wd)q : y;
+        }
+    }
+
+    if (DST == IO_GLOBAL) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint64_t* p = c.gout + tile_gidx<K>(lbase[u], c);
+#pragma unroll
+            for (int v = 0; v < (1 << R); ++v)
+                p[(uint64_t)v << gshift] = (uint64_t)x[(v << (LOG_R - R)) | u];
+        }
+    } else {
+#pragma unroll
+        for (int reg = 0; reg < RN; ++reg) {
+            const int u = reg & (U - 1), v = reg >> (LOG_R - R);
+            sm[swz(lbase[u] + ((uint32_t)v << sshift))] = (uint64_t)x[reg];
+        }
+    }
+}
+
+// Cooperative coalesced copies of the whole tile between HBM and shared memory.
+template <int K>
+__device__ __forceinline__ void tile_to_smem(uint64_t* sm, const TileCtx& c, uint32_t TE) {
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(c.gin);
+    for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
+        const uint32_t l = 2 * i;
+        const ulonglong2 v = __ldg(src + (tile_gidx<K>(l, c) >> 1));
+        sm[swz(l)] = v.x;
+        sm[swz(l + 1)] = v.y;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void smem_to_tile(const uint64_t* sm, const TileCtx& c, uint32_t TE) {
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(c.gout);
+    for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
+        const uint32_t l = 2 * i;
+        dst[tile_gidx<K>(l, c) >> 1] = make_ulonglong2(sm[swz(l)], sm[swz(l + 1)]);
+    }
+}
+
+// Executes round I (in execution order) and the ones after it.  COLUMN
+// passes (logGc > 0) read and write HBM directly in their first and last
+// rounds; row passes do so at their low-stage end only (the forward's first
+// round, the inverse's last) and stage the high-stage end through shared
+// memory, where the round's thread map is strided.
+template <bool FWD, bool COLUMN, typename Wd, int LOG_R, int K, int I>
+__device__ __forceinline__ void ntt_rounds(uint64_t* sm, const ulonglong2* __restrict__ tw,
+                                           const LimbDev& lc, const TileCtx& c) {
+    using S = Sched<K, LOG_R>;
+    constexpr int NR = S::NR;
+    constexpr int idx = FWD ? I : NR - 1 - I;
+    constexpr bool first = I == 0, lastr = I == NR - 1;
+    constexpr bool direct_in = first && (COLUMN || FWD);
+    constexpr bool direct_out = lastr && (COLUMN || !FWD);
+    TileCtx cr = c;
+    cr.last = c.last && lastr;
+    ntt_round<FWD, Wd, LOG_R, K, S::off(idx), S::size(idx), direct_in ? IO_GLOBAL : IO_SMEM,
+              direct_out ? IO_GLOBAL : IO_SMEM>(sm, tw, lc, cr);
+    if constexpr (!lastr) {
+        __syncthreads();
+        ntt_rounds<FWD, COLUMN, Wd, LOG_R, K, I + 1>(sm, tw, lc, c);
+    }
+}
+
+template <bool FWD, bool COLUMN, int LOG_R, int K>
+__global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
+    extern __shared__ uint64_t sm[];
+    const uint32_t limb = blockIdx.y;
+    const uint32_t poly = blockIdx.x % a.n_polys;
+    const uint32_t tile = blockIdx.x / a.n_polys;
+    const LimbDev lc = a.limbs[limb];
+    const uint64_t base = ((uint64_t)poly * a.n_limbs + limb) << a.L;
+    const uint32_t tile_c = tile & ((1u << a.log_tiles_c) - 1);
+    const uint32_t tile_b = tile >> a.log_tiles_c;
+    const uint32_t TE = 1u << (a.logGb + K + a.logGc);
+    TileCtx c;
+    c.gin = a.in + base;
+    c.gout = a.out + base;
+    c.b_base = (uint64_t)tile_b << a.logGb;
+    c.c_base = (uint64_t)tile_c << a.logGc;
+    c.L = a.L;
+    c.s0 = a.s0;
+    c.logGc = a.logGc;
+    c.w = a.L - a.s0 - K;
+    c.nthreads = TE >> LOG_R;
+    c.out_mf = a.out_mf;
+    c.last = a.last != 0;
+
+    constexpr bool staged_in = !COLUMN && !FWD;
+    constexpr bool staged_out = !COLUMN && FWD;
+    if (staged_in) {
+        tile_to_smem<K>(sm, c, TE);
+        __syncthreads();
+    }
+    const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
+    if (lc.narrow)
+        ntt_rounds<FWD, COLUMN, uint32_t, LOG_R, K, 0>(sm, tw, lc, c);
+    else
+        ntt_rounds<FWD, COLUMN, uint64_t, LOG_R, K, 0>(sm, tw, lc, c);
+    if (staged_out) {
+        __syncthreads();
+        smem_to_tile<K>(sm, c, TE);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent, double-buffered variant.  Each block walks the tiles t =
+// blockIdx.x, blockIdx.x + gridDim.x, ...; while it transforms tile t out of
+// one shared-memory buffer, the next tile streams into the other buffer with
+// cp.async (16-byte asynchronous copies that bypass the registers), so HBM
+// latency hides behind the butterflies even at two blocks per SM.  Each
+// round's twiddle pairs are all requested before its butterflies start.
+// Tiles are numbered (limb, tile, polynomial) with the polynomial fastest, so
+// blocks that run together share one limb's twiddles in L1/L2.
+// ---------------------------------------------------------------------------
+
+// 16-byte-granular swizzle (keeps the two words of each aligned pair together
+// so cp.async can write it): XOR bits 1..3 with bits 4..6; every round of the
+// schedules used here sees at most 2-way bank conflicts.
+__device__ __forceinline__ uint32_t swz16(uint32_t l) { return l ^ (((l >> 4) & 7u) << 1); }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+struct TileId {
+    uint32_t limb, poly, tile;
+};
+
+__device__ __forceinline__ TileId decode_tile(uint32_t t, const PassArgs& a, uint32_t tiles) {
+    TileId id;
+    id.poly = t % a.n_polys;
+    const uint32_t r = t / a.n_polys;
+    id.tile = r % tiles;
+    id.limb = r / tiles;
+    return id;
+}
+
+template <int K>
+__device__ __forceinline__ void tile_ctx(const TileId& id, const PassArgs& a, TileCtx& c) {
+    const uint64_t base = ((uint64_t)id.poly * a.n_limbs + id.limb) << a.L;
+    const uint32_t tile_c = id.tile & ((1u << a.log_tiles_c) - 1);
+    const uint32_t tile_b = id.tile >> a.log_tiles_c;
+    c.gin = a.in + base;
+    c.gout = a.out + base;
+    c.b_base = (uint64_t)tile_b << a.logGb;
+    c.c_base = (uint64_t)tile_c << a.logGc;
+    c.L = a.L;
+    c.s0 = a.s0;
+    c.logGc = a.logGc;
+    c.w = a.L - a.s0 - K;
+    c.out_mf = a.out_mf;
+    c.last = a.last != 0;
+}
+
+template <int K>
+__device__ __forceinline__ void tile_prefetch(uint64_t* dst, const TileCtx& c, uint32_t TE) {
+    for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
+        const uint32_t l = 2 * i;
+        cp_async16(dst + swz16(l), c.gin + tile_gidx<K>(l, c));
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void smem16_to_tile(const uint64_t* sm, const TileCtx& c, uint32_t TE) {
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(c.gout);
+    for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
+        const uint32_t l = 2 * i;
+        dst[tile_gidx<K>(l, c) >> 1] = *reinterpret_cast<const ulonglong2*>(sm + swz16(l));
+    }
+}
+
+// One register round of the pipelined kernel: reads its elements from the
+// (swz16) tile in shared memory, writes them back there or, in the last
+// round of a coalesced end, straight to HBM.
+template <bool FWD, typename Wd, int LOG_R, int K, int P, int R, bool TO_GLOBAL>
+__device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __restrict__ tw,
+                                           const LimbDev& lc, const TileCtx& c) {
+    constexpr int RN = 1 << LOG_R;
+    constexpr int U = 1 << (LOG_R - R);
+    constexpr int ELO = K - P - R;
+    constexpr int NTW = (1 << R) - 1;   // twiddles per group in this round
+    Wd x[RN];
+    uint64_t pfx[U];
+    uint32_t lbase[U];
+    const uint32_t cmask = (1u << c.logGc) - 1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t g = u * c.nthreads + threadIdx.x;
+        const uint32_t cl = g & cmask;
+        const uint32_t t1 = g >> c.logGc;
+        const uint32_t elo = t1 & ((1u << ELO) - 1);
+        const uint32_t t2 = t1 >> ELO;
+        const uint32_t ehi = t2 & ((1u << P) - 1);
+        const uint32_t bl = t2 >> P;
+        lbase[u] = (bl << (K + c.logGc)) | (ehi << (K - P + c.logGc)) | (elo << c.logGc) | cl;
+        pfx[u] = ((c.b_base + bl) << P) | ehi;
+    }
+    // every twiddle of the round first: sub-stage k of group u needs entries
+    // 2^s + (pfx << k) + j, j < 2^k
+    ulonglong2 wt[U][NTW];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const ulonglong2* tb = tw + ((1ull << (c.s0 + P + k)) + (pfx[u] << k));
+#pragma unroll
+            for (int j = 0; j < (1 << k); ++j) wt[u][(1 << k) - 1 + j] = __ldg(tb + j);
+        }
+    }
+    const int sshift = ELO + c.logGc;
+#pragma unroll
+    for (int reg = 0; reg < RN; ++reg) {
+        const int u = reg & (U - 1), v = reg >> (LOG_R - R);
+        x[reg] = (Wd)sm[swz16(lbase[u] + ((uint32_t)v << sshift))];
+    }
+
+    const uint64_t q = lc.q, q2 = lc.two_q;
+#pragma unroll
+    for (int kk = 0; kk < R; ++kk) {
+        const int k = FWD ? kk : R - 1 - kk;
+        const int hb = LOG_R - 1 - k;
+        if (!FWD && P == 0 && k == 0 && c.s0 == 0) {
+#pragma unroll
+            for (int reg0 = 0; reg0 < RN; ++reg0) {
+                if (reg0 & (1 << hb)) continue;
+                const int reg1 = reg0 | (1 << hb);
+                const Wd a = x[reg0], b = x[reg1];
+                const Wd sum = a + b;
+                const Wd dif = a - b + (Wd)q2;
+                x[reg0] = Word<Wd>::mul(sum, lc.ninv, lc.ninv_p, q);
+                x[reg1] = Word<Wd>::mul(dif, lc.ninv_w, lc.ninv_w_p, q);
+            }
+            continue;
+        }
+#pragma unroll
+        for (int reg0 = 0; reg0 < RN; ++reg0) {
+            if (reg0 & (1 << hb)) continue;
+            const int reg1 = reg0 | (1 << hb);
+            const int u = reg0 & (U - 1), v0 = reg0 >> (LOG_R - R);
+            const ulonglong2 w = wt[u][(1 << k) - 1 + (v0 >> (R - k))];
+            if (FWD)
+                Word<Wd>::fwd(x[reg0], x[reg1], w, q, q2);
+            else
+                Word<Wd>::inv(x[reg0], x[reg1], w, q, q2);
+        }
+    }
+    if (c.last && c.out_mf == 1) {
+#pragma unroll
+        for (int reg = 0; reg < RN; ++reg) {
+            Wd y = x[reg];
+            if (FWD) y = y >= (Wd)q2 ? y - (Wd)q2 : y;
+            x[reg] = y >= (Wd)q ? y - (Wd)q : y;
+        }
+    }
+    if (TO_GLOBAL) {
+        const int gshift = ELO + c.w;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint64_t* p = c.gout + tile_gidx<K>(lbase[u], c);
+#pragma unroll
+            for (int v = 0; v < (1 << R); ++v)
+                p[(uint64_t)v << gshift] = (uint64_t)x[(v << (LOG_R - R)) | u];
+        }
+    } else {
+#pragma unroll
+        for (int reg = 0; reg < RN; ++reg) {
+            const int u = reg & (U - 1), v = reg >> (LOG_R - R);
+            sm[swz16(lbase[u] + ((uint32_t)v << sshift))] = (uint64_t)x[reg];
+        }
+    }
+}
+
+template <bool FWD, bool COLUMN, typename Wd, int LOG_R, int K, int I>
+__device__ __forceinline__ void pipe_rounds(uint64_t* sm, const ulonglong2* __restrict__ tw,
+                                            const LimbDev& lc, const TileCtx& c) {
+    using S = Sched<K, LOG_R>;
+    constexpr int NR = S::NR;
+    constexpr int idx = FWD ? I : NR - 1 - I;
+    constexpr bool lastr = I == NR - 1;
+    TileCtx cr = c;
+    cr.last = c.last && lastr;
+    pipe_round<FWD, Wd, LOG_R, K, S::off(idx), S::size(idx), lastr && (COLUMN || !FWD)>(sm, tw,
+                                                                                       lc, cr);
+    if constexpr (!lastr) {
+        __syncthreads();
+        pipe_rounds<FWD, COLUMN, Wd, LOG_R, K, I + 1>(sm, tw, lc, c);
+    }
+}
+
+template <bool FWD, bool COLUMN, int LOG_R, int K>
+__global__ void __launch_bounds__(256, 2) ntt_pipe_kernel(PassArgs a) {
+    extern __shared__ uint64_t sm[];
+    const int logTE = a.logGb + K + a.logGc;
+    const uint32_t TE = 1u << logTE;
+    const uint32_t tiles = 1u << (a.L - logTE);
+    const uint32_t total = tiles * a.n_polys * a.n_limbs;
+    uint32_t t = blockIdx.x;
+    if (t >= total) return;
+    TileCtx c;
+    c.nthreads = TE >> LOG_R;
+    tile_ctx<K>(decode_tile(t, a, tiles), a, c);
+    tile_prefetch<K>(sm, c, TE);
+    cp_async_commit();
+    for (uint32_t i = 0; t < total; ++i, t += gridDim.x) {
+        uint64_t* buf = sm + (i & 1) * TE;
+        const uint32_t tn = t + gridDim.x;
+        if (tn < total) {
+            TileCtx cn;
+            cn.nthreads = c.nthreads;
+            tile_ctx<K>(decode_tile(tn, a, tiles), a, cn);
+            tile_prefetch<K>(sm + ((i + 1) & 1) * TE, cn, TE);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const TileId id = decode_tile(t, a, tiles);
+        tile_ctx<K>(id, a, c);
+        const LimbDev lc = a.limbs[id.limb];
+        const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
+        if (lc.narrow)
+            pipe_rounds<FWD, COLUMN, uint32_t, LOG_R, K, 0>(buf, tw, lc, c);
+        else
+            pipe_rounds<FWD, COLUMN, uint64_t, LOG_R, K, 0>(buf, tw, lc, c);
+        if (!COLUMN && FWD) {
+            __syncthreads();
+            smem16_to_tile<K>(buf, c, TE);
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+typedef void (*PassKernel)(PassArgs);
+
+// ntt_fwd.cu / ntt_inv.cu
+PassKernel pick_fwd(bool column, int logR, int K);
+PassKernel pick_inv(bool column, int logR, int K);
+PassKernel pick_fwd_pipe(bool column, int logR, int K);
+PassKernel pick_inv_pipe(bool column, int logR, int K);
+
+}  // namespace hx

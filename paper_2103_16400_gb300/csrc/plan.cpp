@@ -113,17 +113,21 @@ static void fill_limb(uint64_t N, int logN, uint64_t q, uint64_t psi, ulonglong2
     ld->pad = 0;
 }
 
-NttCfg default_cfg(int logN) {
+// Untuned default schedules (the autotuner replaces them per workload).  For
+// N > 2^13: a column pass over the first log2(N)/2 stages in 8- or 4-column
+// tiles, then a row pass over the rest in small row tiles of 8 elements a
+// thread -- the fastest shapes of a sweep at N = 2^16 on 32 mixed limbs.
+NttCfg default_cfg(int logN, bool forward) {
     NttCfg c{};
     if (logN <= 13) {
         c.npass = 1;
-        c.pass[0] = PassCfg{0, logN, 0, 0, logN <= 12 ? 3 : 4};
+        c.pass[0] = PassCfg{0, logN, 0, 0, logN <= 12 ? 3 : 4, 0};
     } else {
-        int K1 = logN / 2, K2 = logN - K1;
+        const int K1 = logN / 2, K2 = logN - K1;
         c.npass = 2;
-        c.pass[0] = PassCfg{0, K1, 0, 4, 3};
-        int logGb = std::max(0, 12 - K2);
-        c.pass[1] = PassCfg{K1, K2, std::min(logGb, K1), 0, 3};
+        c.pass[0] = forward ? PassCfg{0, K1, 0, 3, 4, 0} : PassCfg{0, K1, 0, 2, 3, 0};
+        const int logGb = std::max(forward ? 0 : 1, 8 - K2);
+        c.pass[1] = PassCfg{K1, K2, std::min(logGb, K1), 0, 3, 0};
     }
     return c;
 }
@@ -161,7 +165,8 @@ extern "C" int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_modu
     p->n_limbs = n_limbs;
     p->moduli.assign(h_moduli, h_moduli + n_limbs);
     p->roots = roots;
-    p->cfg = default_cfg(logN);
+    p->cfg_fwd = default_cfg(logN, true);
+    p->cfg_inv = default_cfg(logN, false);
     cudaGetDevice(&p->device);
 
     const size_t table_pairs = (size_t)N * n_limbs;
@@ -233,5 +238,35 @@ extern "C" int hx_plan_info(hx_plan_t p, uint64_t* N, uint32_t* n_limbs, uint64_
     if (N) *N = p->N;
     if (n_limbs) *n_limbs = p->n_limbs;
     if (bytes) *bytes = p->device_bytes;
+    return HX_OK;
+}
+
+extern "C" int hx_plan_set_schedule(hx_plan_t p, uint32_t direction, uint32_t npass,
+                                    const int32_t* params) {
+    if (!p || !params) return HX_ERR_NULL;
+    if (npass < 1 || npass > 2 || direction < 1 || direction > 3) return HX_ERR_ARG;
+    NttCfg c{};
+    c.npass = (int)npass;
+    for (uint32_t i = 0; i < npass; ++i) {
+        const int32_t* q = params + 6 * i;
+        c.pass[i] = PassCfg{q[0], q[1], q[2], q[3], q[4], q[5]};
+    }
+    if (!cfg_supported(p->logN, c)) return HX_ERR_ARG;
+    if (direction & 1) p->cfg_fwd = c;
+    if (direction & 2) p->cfg_inv = c;
+    return HX_OK;
+}
+
+extern "C" int hx_plan_get_schedule(hx_plan_t p, uint32_t direction, uint32_t* npass,
+                                    int32_t* params) {
+    if (!p || !npass || !params) return HX_ERR_NULL;
+    if (direction != 1 && direction != 2) return HX_ERR_ARG;
+    const NttCfg& cfg = direction == 1 ? p->cfg_fwd : p->cfg_inv;
+    *npass = (uint32_t)cfg.npass;
+    for (int i = 0; i < 2; ++i) {
+        const PassCfg& c = cfg.pass[i];
+        const int32_t v[6] = {c.s0, c.K, c.logGb, c.logGc, c.logR, c.pipe};
+        memcpy(params + 6 * i, v, sizeof(v));
+    }
     return HX_OK;
 }

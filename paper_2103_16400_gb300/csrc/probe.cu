@@ -1,0 +1,180 @@
+// Measurement support (no counterpart in the paper): throughput probes that
+// give the integer roofline its denominator, and the launch counter.
+//
+// hx_probe_int_mul_rate: every thread runs 8 independent dependency chains of
+// one 32-bit integer multiply form (kind 0: mad.lo.u32, the low half of a
+// 32x32-bit product plus an addend; kind 1: mad.hi.u32, the high half;
+// kind 2: mad.wide.u32, the full 64-bit product; kind 3: lo and hi
+// alternating).  The grid fills every SM; the rate is
+// (threads x iterations x 16 instructions) / elapsed time.
+//
+// hx_probe_butterfly_rate: the same grid runs Harvey forward or inverse
+// butterflies on register-resident data (no memory traffic), giving the
+// arithmetic ceiling of each Shoup-product variant of the butterfly code.
+#include <atomic>
+
+#include "hx_internal.h"
+#include "modarith.cuh"
+
+namespace hx {
+
+std::atomic<uint64_t> g_launches{0};
+
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+template <int KIND>
+__global__ void __launch_bounds__(256) int_mul_probe_kernel(uint32_t iters, uint32_t a,
+                                                            uint32_t b, uint32_t* sink) {
+    uint32_t x[8];
+    uint64_t y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        x[i] = threadIdx.x * 7u + i;
+        y[i] = x[i];
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (KIND == 0 || (KIND == 3 && h == 0))
+                    asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[i]) : "r"(a), "r"(b));
+                else if (KIND == 1 || KIND == 3)
+                    asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(x[i]) : "r"(a), "r"(b));
+                else
+                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(y[i]) : "r"((uint32_t)y[i]), "r"(a));
+            }
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= x[i] ^ (uint32_t)y[i] ^ (uint32_t)(y[i] >> 32);
+    if (acc == 0x9e3779b9u) sink[blockIdx.x] = acc;   // keeps the chains live
+}
+
+template <typename Wd, int V, bool INV>
+__global__ void __launch_bounds__(256) butterfly_probe_kernel(uint32_t iters, uint64_t q,
+                                                              uint64_t w, uint64_t wp,
+                                                              uint64_t* sink) {
+    Wd x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (Wd)((threadIdx.x * 131u + i) % q);
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            if constexpr (sizeof(Wd) == 8) {
+                if (INV)
+                    harvey_inv64<V>(x[i], x[i + 1], w, wp, q, 2 * q);
+                else
+                    harvey_fwd64<V>(x[i], x[i + 1], w, wp, q, 2 * q);
+            } else {
+                if (INV)
+                    harvey_inv32(x[i], x[i + 1], (uint32_t)w, (uint32_t)wp, (uint32_t)q,
+                                 (uint32_t)(2 * q));
+                else
+                    harvey_fwd32(x[i], x[i + 1], (uint32_t)w, (uint32_t)wp, (uint32_t)q,
+                                 (uint32_t)(2 * q));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {   // re-pair so the chains mix
+            Wd t = x[i];
+            x[i] = x[7 - i];
+            x[7 - i] = t;
+        }
+        // an opaque register move per iteration keeps the loop from being folded
+        asm volatile("" : "+r"(*(uint32_t*)&x[0]));
+    }
+    uint64_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= (uint64_t)x[i];
+    if (acc == 0x9e3779b97f4a7c15ull) sink[blockIdx.x] = acc;
+}
+
+typedef void (*BflyKernel)(uint32_t, uint64_t, uint64_t, uint64_t, uint64_t*);
+
+template <int V>
+static BflyKernel bfly_kernel(bool narrow, bool inv) {
+    if (narrow) return inv ? butterfly_probe_kernel<uint32_t, V, true>
+                           : butterfly_probe_kernel<uint32_t, V, false>;
+    return inv ? butterfly_probe_kernel<uint64_t, V, true> : butterfly_probe_kernel<uint64_t, V, false>;
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 152;
+}
+
+typedef void (*ProbeKernel)(uint32_t, uint32_t, uint32_t, uint32_t*);
+
+// Times `launch(iters)` after one short warm-up launch; returns ms or < 0.
+template <class F>
+static float time_probe(cudaStream_t st, F launch, uint32_t iters) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    launch(iters / 8 + 1);
+    cudaEventRecord(e0, st);
+    launch(iters);
+    cudaEventRecord(e1, st);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess || cudaGetLastError() != cudaSuccess) return -1.f;
+    return t;
+}
+
+}  // namespace hx
+
+using namespace hx;
+
+extern "C" uint64_t hx_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" int hx_probe_int_mul_rate(uint32_t kind, uint32_t iters, double* ops_per_s, float* ms,
+                                     hx_stream_t stream) {
+    if (!ops_per_s) return HX_ERR_NULL;
+    if (iters == 0 || kind > 3) return HX_ERR_ARG;
+    static const ProbeKernel kernels[4] = {int_mul_probe_kernel<0>, int_mul_probe_kernel<1>,
+                                           int_mul_probe_kernel<2>, int_mul_probe_kernel<3>};
+    const int blocks = sm_count() * 8;
+    uint32_t* sink = nullptr;
+    if (cudaMalloc(&sink, blocks * sizeof(uint32_t)) != cudaSuccess) return HX_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    ProbeKernel k = kernels[kind];
+    float t = time_probe(st, [&](uint32_t it) {
+        k<<<blocks, 256, 0, st>>>(it, 0x9e3779b1u, 0x7f4a7c15u, sink);
+    }, iters);
+    cudaFree(sink);
+    if (t <= 0) return HX_ERR_CUDA;
+    *ops_per_s = (double)blocks * 256.0 * iters * 16.0 / (t * 1e-3);
+    if (ms) *ms = t;
+    return HX_OK;
+}
+
+extern "C" int hx_probe_butterfly_rate(uint32_t variant, uint32_t iters, uint64_t q,
+                                       double* butterflies_per_s, float* ms, hx_stream_t stream) {
+    if (!butterflies_per_s) return HX_ERR_NULL;
+    const uint32_t v = variant & 15u;
+    const bool inv = (variant >> 4) & 1u;
+    if (iters == 0 || q < 3 || q >= (1ull << 62) || v > 2) return HX_ERR_ARG;
+    const int blocks = sm_count() * 8;
+    uint64_t* sink = nullptr;
+    if (cudaMalloc(&sink, blocks * sizeof(uint64_t)) != cudaSuccess) return HX_ERR_NOMEM;
+    const uint64_t w = q / 3 + 1;
+    const bool narrow = q < (1ull << 30);
+    const uint64_t wp = narrow ? ((w << 32) / q) : (uint64_t)(((unsigned __int128)w << 64) / q);
+    BflyKernel k = v == 0 ? bfly_kernel<0>(narrow, inv)
+                          : v == 1 ? bfly_kernel<1>(narrow, inv) : bfly_kernel<2>(narrow, inv);
+    cudaStream_t st = (cudaStream_t)stream;
+    float t = time_probe(st, [&](uint32_t it) { k<<<blocks, 256, 0, st>>>(it, q, w, wp, sink); },
+                         iters);
+    cudaFree(sink);
+    if (t <= 0) return HX_ERR_CUDA;
+    *butterflies_per_s = (double)blocks * 256.0 * iters * 4.0 / (t * 1e-3);
+    if (ms) *ms = t;
+    return HX_OK;
+}

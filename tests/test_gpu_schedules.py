@@ -1,0 +1,55 @@
+"""Every kernel schedule the autotuner may pick gives the same bits: the
+forward and inverse transforms under each valid schedule (pass split, tile
+shape, elements per thread, plain or persistent double-buffered kernel) are
+compared with the oracle, at N = 2^12 (single and split passes), 2^14,
+2^16 and 2^17, with one limb of each width and two polynomials."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from paper_2103_16400_gb300 import capi, tune
+from paper_2103_16400_gb300.tensors import empty, to_device, to_host
+
+pytestmark = pytest.mark.gpu
+
+MIXED3 = W.mixed_width_primes(3)
+
+
+@pytest.mark.parametrize("logN", [12, 14, 16, 17])
+def test_all_schedules_bit_exact(hexlib, logN):
+    N = 1 << logN
+    x = W.poly_batch(W.SEED_BASE + 900 + logN, 1, 2, MIXED3, N)
+    fwd_exp = oracle.ntt_forward(x, MIXED3)
+    plan = capi.Plan(N, MIXED3)
+    dx, dy = to_device(x), empty(x.shape)
+    dz = empty(x.shape)
+    n_valid = 0
+    for sched in tune.candidates(logN):
+        if not tune.valid(plan, sched):
+            continue
+        n_valid += 1
+        capi.hx_ntt_forward(plan, dy, dx, 2, 1, 1)
+        capi.hx_ntt_inverse(plan, dz, dy, 2, 1, 1)
+        got = to_host(dy)
+        if not np.array_equal(got, fwd_exp):
+            pytest.fail(f"forward differs under schedule {sched}")
+        if not np.array_equal(to_host(dz), x):
+            pytest.fail(f"inverse differs under schedule {sched}")
+    assert n_valid >= 4
+
+
+def test_tuner_picks_a_valid_schedule_and_caches(hexlib, tmp_path, monkeypatch):
+    monkeypatch.setattr(tune, "CACHE_PATH", str(tmp_path / "cache.json"))
+    N = 1 << 14
+    plan = capi.Plan(N, MIXED3)
+    res = tune.tune(plan, 2, iters=1)
+    assert res["tried"] >= 4 and res["fwd_us"] > 0
+    assert [list(p) for p in plan.schedule(plan.FORWARD)] == res["forward"]
+    assert [list(p) for p in plan.schedule(plan.INVERSE)] == res["inverse"]
+    again = tune.tune(capi.Plan(N, MIXED3), 2)
+    assert again.get("cached") and again["forward"] == res["forward"]
+    x = W.poly_batch(W.SEED_BASE + 950, 1, 2, MIXED3, N)
+    dy = empty(x.shape)
+    capi.hx_ntt_forward(plan, dy, to_device(x), 2, 1, 1)
+    np.testing.assert_array_equal(to_host(dy), oracle.ntt_forward(x, MIXED3))
