@@ -120,6 +120,65 @@ class HexStep:
         return [R[0:1], R[1:2], R[2:3]]
 
 
+# ------------------------------------------------------------------ ragged batch
+def ragged_report(torch, n_polys=512, reps=5):
+    """The ragged workload (N ~ U{2^10..2^17}, 1-32 limbs of 30/50/60 bits):
+    forward NTT of every polynomial as one graph replay of the persistent
+    ragged kernels, against one plain launch per (polynomial, limb) and one
+    call per polynomial; outputs of all three are compared on the device."""
+    from paper_2103_16400_gb300 import capi
+    from paper_2103_16400_gb300.tensors import empty, to_device
+    entries = W.ragged_batch(n_polys)
+    plans, dins, douts, dref, dref2 = [], [], [], [], []
+    for k, (N, qs) in enumerate(entries):
+        x = W.poly_batch(W.SEED_BASE + 4, k, 1, qs, N)
+        plans.append(capi.Plan(N, qs))
+        dins.append(to_device(x))
+        douts.append(empty(x.shape))
+        dref.append(empty(x.shape))
+        dref2.append(empty(x.shape))
+    batch = capi.Batch([(p, i, o, 1) for p, i, o in zip(plans, dins, douts)], 1, 1, 1)
+    info = batch.info()
+    one_limb = {}
+    for (N, qs) in entries:
+        for q in qs:
+            if (N, q) not in one_limb:
+                one_limb[(N, q)] = capi.Plan(N, [q])
+    st = torch.cuda.current_stream()
+
+    def per_limb():
+        for (N, qs), i, o in zip(entries, dins, dref):
+            for l, q in enumerate(qs):
+                capi.hx_ntt_forward(one_limb[(N, q)], o[0, l], i[0, l], 1, 1, 1, st)
+
+    def per_poly():
+        for p, i, o in zip(plans, dins, dref2):
+            capi.hx_ntt_forward(p, o, i, 1, 1, 1, st)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_batch = timed(lambda: batch.run(st))
+    t_limb = timed(per_limb)
+    t_poly = timed(per_poly)
+    same = all(torch.equal(a, b) and torch.equal(a, c) for a, b, c in zip(douts, dref, dref2))
+    lt = info["limb_transforms"]
+    return {"workload": f"ragged_{n_polys}_polys_N2^10..2^17_1-32_limbs",
+            "limb_transforms": lt, "tiles": info["tiles"], "launches_per_replay": info["launches"],
+            "batch_ms": t_batch, "batch_limb_transforms_per_s": lt / (t_batch * 1e-3),
+            "per_limb_launch_ms": t_limb, "per_limb_limb_transforms_per_s": lt / (t_limb * 1e-3),
+            "per_poly_call_ms": t_poly, "per_poly_limb_transforms_per_s": lt / (t_poly * 1e-3),
+            "speedup_vs_per_limb": t_limb / t_batch, "bit_exact_equal": bool(same)}
+
+
 # ------------------------------------------------------------------ clocks
 _REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
             0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
@@ -344,6 +403,8 @@ def main():
     ap.add_argument("--limbs", type=int, default=LIMBS_DEFAULT)
     ap.add_argument("--sets", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true",
+                    help="skip the ragged-batch report (512 polynomials, mixed N)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--case", default="pipeline",
                     choices=["pipeline", "fwd", "inv", "tensor", "probes"],
@@ -469,6 +530,8 @@ def main():
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks.summary()}
+    if not args.no_ragged:
+        line["batched"] = ragged_report(torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(N, wl.moduli, s, sets)
     if rank == 0:

@@ -226,6 +226,51 @@ int hx_dyadic_tensor_fma(uint64_t* d_r0, uint64_t* d_r1, uint64_t* d_r2, const u
                          uint32_t n_limbs, uint32_t n_polys, uint32_t input_mod_factor,
                          hx_stream_t stream);
 
+/* -------------------------------------------------------------- ragged batches
+ * Many transforms of different N and modulus sets in one replay: the
+ * paper's per-call NTT (Section 3) is too small to fill a GPU by itself
+ * (Section 4 notes the offload problem), so a batch gathers every
+ * (polynomial, limb) transform of every item into one tile list and runs it
+ * as one persistent kernel per pass, captured once into a CUDA graph.
+ *
+ * hx_ragged_item: one group of polynomials sharing a plan.
+ *   plan     the plan (N and moduli) of these polynomials
+ *   d_in     device operand [n_polys][plan n_limbs][N]
+ *   d_out    device result, same shape; equal to d_in or disjoint
+ *   n_polys  >= 1
+ *
+ * hx_batch_create(out, h_items, n_items, direction, input_mod_factor,
+ *                 output_mod_factor)
+ *   h_items  host array of n_items items (read during the call only); the
+ *            plans and device buffers must outlive the batch.
+ *   direction 1 = forward (input_mod_factor 1/2/4, output 1/4),
+ *             2 = inverse (input 1/2, output 1/2); the same semantics as
+ *             hx_ntt_forward / hx_ntt_inverse per transform.
+ *   Allocates the tile list (32 bytes per 2048-element tile) and two work
+ *   counters in device memory on the current device, and instantiates the
+ *   graph.  Errors: HX_ERR_NULL, HX_ERR_ALIGN, HX_ERR_ARG, HX_ERR_MOD_FACTOR,
+ *   HX_ERR_OVERLAP, HX_ERR_NOMEM, HX_ERR_CUDA.
+ * hx_batch_run: enqueues one replay of the whole batch on `stream` (one
+ *   graph launch: counter reset, then one or two persistent passes).
+ *   Replays on different streams must not overlap in time (they share the
+ *   counters).
+ * hx_batch_info: transforms, tiles and kernel launches per replay.
+ */
+typedef struct hx_ragged_item {
+    hx_plan_t plan;
+    const uint64_t* d_in;
+    uint64_t* d_out;
+    uint32_t n_polys;
+    uint32_t reserved;
+} hx_ragged_item;
+
+int hx_batch_create(hx_batch_t* out, const hx_ragged_item* h_items, uint32_t n_items,
+                    uint32_t direction, uint32_t input_mod_factor, uint32_t output_mod_factor);
+int hx_batch_run(hx_batch_t batch, hx_stream_t stream);
+int hx_batch_info(hx_batch_t batch, uint64_t* limb_transforms, uint64_t* tiles,
+                  uint32_t* launches);
+int hx_batch_destroy(hx_batch_t batch);
+
 /* ---------------------------------------------------------------- measurement
  * Support for the benchmark; the paper has no counterpart.
  *

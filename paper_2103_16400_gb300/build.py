@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhexgpu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "capi.cpp", "ntt.cu", "ntt_fwd.cu", "ntt_inv.cu", "eltwise.cu", "probe.cu"]
+SOURCES = ["plan.cpp", "capi.cpp", "ntt.cu", "ntt_fwd.cu", "ntt_inv.cu", "eltwise.cu", "probe.cu",
+           "batch.cu"]
 
 
 def nvcc() -> str:

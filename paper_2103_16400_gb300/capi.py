@@ -42,6 +42,10 @@ _SIGS = {
     "hx_ciphertext_tensor": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, VP],
     "hx_dyadic_tensor_fma": [VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U64, P64, U32, U32,
                              U32, VP],
+    "hx_batch_create": [ctypes.POINTER(VP), VP, U32, U32, U32, U32],
+    "hx_batch_run": [VP, VP],
+    "hx_batch_info": [VP, P64, P64, ctypes.POINTER(U32)],
+    "hx_batch_destroy": [VP],
     "hx_launch_count": [],
     "hx_probe_int_mul_rate": [U32, U32, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_float), VP],
@@ -167,6 +171,49 @@ class Plan:
 
 def _h(plan):
     return plan.handle if isinstance(plan, Plan) else plan
+
+
+class RaggedItem(ctypes.Structure):
+    """hx_ragged_item: polynomials sharing one plan, in a ragged batch."""
+    _fields_ = [("plan", VP), ("d_in", VP), ("d_out", VP), ("n_polys", U32),
+                ("reserved", U32)]
+
+
+class Batch:
+    """Owns an hx_batch_t: a ragged set of transforms replayed as one graph.
+    items: iterable of (plan, d_in, d_out, n_polys)."""
+
+    def __init__(self, items, direction: int = 1, input_mod_factor: int = 1,
+                 output_mod_factor: int = 1):
+        items = list(items)
+        arr = (RaggedItem * len(items))(*[RaggedItem(_h(p), ptr(i), ptr(o), n, 0)
+                                          for p, i, o, n in items])
+        self._keep = items                      # plans and buffers outlive the batch
+        h = VP()
+        _check("hx_batch_create", load().hx_batch_create(
+            ctypes.byref(h), ctypes.cast(arr, VP), len(items), direction, input_mod_factor,
+            output_mod_factor))
+        self.handle = h.value
+
+    def run(self, stream=None):
+        _check("hx_batch_run", load().hx_batch_run(self.handle, _stream(stream)))
+
+    def info(self):
+        lt, tiles, launches = U64(), U64(), U32()
+        _check("hx_batch_info", load().hx_batch_info(self.handle, ctypes.byref(lt),
+                                                     ctypes.byref(tiles), ctypes.byref(launches)))
+        return {"limb_transforms": lt.value, "tiles": tiles.value, "launches": launches.value}
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            _check("hx_batch_destroy", load().hx_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------- entry points

@@ -1,0 +1,273 @@
+// Ragged batches: many transforms of different N (2^10 .. 2^17) and different
+// modulus sets run as one persistent kernel per pass, replayed as one CUDA
+// graph.
+//
+// Every transform is cut into tiles of 2048 elements (1024 at N = 2^10) from a
+// fixed menu of pass shapes, one per log2 N:
+//   N = 2^10, 2^11      one pass over all stages (S10, S11)
+//   N = 2^12 .. 2^17    a column pass over the first K1 stages (C5..C8) and a
+//                       row pass over the last K2 (R7..R9), K1 + K2 = log2 N
+// The host writes one 32-byte descriptor per tile (operand and result
+// pointers, the limb's constants, tile index, menu entry); a persistent grid of
+// 256-thread blocks takes tiles from the list through an atomic counter, so
+// blocks that draw small or narrow tiles simply take more of them.  The
+// second pass of two-pass transforms is a second launch of the same kernel
+// over its own list.  The counters are the batch's only scratch memory; a
+// memset node re-arms them at the head of the graph on every replay.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ntt_kernels.cuh"
+
+namespace hx {
+
+struct RagTile {
+    const uint64_t* in;   // this transform's operand, element 0
+    uint64_t* out;        // this transform's result, element 0
+    const LimbDev* lc;    // its limb constants (twiddle tables inside)
+    uint32_t tile;        // tile index within the pass
+    uint8_t kind;         // menu entry
+    uint8_t L;            // log2 N
+    uint8_t last;         // this pass finishes the transform
+    uint8_t out_mf;
+};
+static_assert(sizeof(RagTile) == 32, "descriptor is 32 bytes");
+
+enum RagKind : uint8_t { RK_S10 = 0, RK_S11, RK_C5, RK_C6, RK_C7, RK_C8, RK_R7, RK_R8, RK_R9 };
+
+// kinds of the first (column or single) and second (row) pass for log2 N
+static void rag_kinds(int L, int* first, int* second) {
+    switch (L) {
+        case 10: *first = RK_S10; *second = -1; break;
+        case 11: *first = RK_S11; *second = -1; break;
+        case 12: *first = RK_C5; *second = RK_R7; break;
+        case 13: *first = RK_C6; *second = RK_R7; break;
+        case 14: *first = RK_C7; *second = RK_R7; break;
+        case 15: *first = RK_C7; *second = RK_R8; break;
+        case 16: *first = RK_C8; *second = RK_R8; break;
+        default: *first = RK_C8; *second = RK_R9; break;   // 17
+    }
+}
+
+// One tile: geometry from the menu, then the same per-tile code as the plain
+// pass kernel.  Tiles hold 2^11 elements (2^10 for S10) in 256 threads.
+template <bool FWD, bool COLUMN, int LOG_R, int K>
+__device__ __forceinline__ void rag_tile(uint64_t* sm, const RagTile& d) {
+    const int L = d.L;
+    const int s0 = COLUMN || K >= L ? 0 : L - K;
+    const int w = L - s0 - K;
+    const int logGc = COLUMN ? 11 - K : 0;
+    const int logGb = COLUMN ? 0 : (K >= L ? 0 : 11 - K);
+    const int logTE = logGb + K + logGc;
+    const int log_tiles_c = w - logGc;
+    TileCtx c;
+    c.gin = d.in;
+    c.gout = d.out;
+    c.b_base = (uint64_t)(d.tile >> log_tiles_c) << logGb;
+    c.c_base = (uint64_t)(d.tile & ((1u << log_tiles_c) - 1)) << logGc;
+    c.L = L;
+    c.s0 = s0;
+    c.logGc = logGc;
+    c.w = w;
+    c.nthreads = (1u << logTE) >> LOG_R;
+    c.out_mf = d.out_mf;
+    c.last = d.last != 0;
+    const LimbDev lc = *d.lc;
+    process_tile<FWD, COLUMN, LOG_R, K>(sm, c, lc, 1u << logTE);
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(256, 2) ragged_pass_kernel(const RagTile* __restrict__ tiles,
+                                                             uint32_t n, uint32_t* counter) {
+    extern __shared__ uint64_t sm[];
+    __shared__ uint32_t s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t t = s_next;
+        if (t >= n) return;
+        const RagTile d = tiles[t];
+        switch (d.kind) {
+            case RK_S10: rag_tile<FWD, false, 2, 10>(sm, d); break;
+            case RK_S11: rag_tile<FWD, false, 3, 11>(sm, d); break;
+            case RK_C5: rag_tile<FWD, true, 3, 5>(sm, d); break;
+            case RK_C6: rag_tile<FWD, true, 3, 6>(sm, d); break;
+            case RK_C7: rag_tile<FWD, true, 3, 7>(sm, d); break;
+            case RK_C8: rag_tile<FWD, true, 3, 8>(sm, d); break;
+            case RK_R7: rag_tile<FWD, false, 3, 7>(sm, d); break;
+            case RK_R8: rag_tile<FWD, false, 3, 8>(sm, d); break;
+            default: rag_tile<FWD, false, 3, 9>(sm, d); break;
+        }
+        __syncthreads();   // tile finished with shared memory and s_next
+    }
+}
+
+static const size_t kRagSmem = 2048 * sizeof(uint64_t);
+
+}  // namespace hx
+
+using namespace hx;
+
+struct hx_batch_s {
+    int device = 0;
+    bool forward = true;
+    uint32_t nA = 0, nB = 0;
+    RagTile* d_tiles = nullptr;     // pass A tiles, then pass B tiles
+    uint32_t* d_counters = nullptr; // [2]
+    int grid = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    uint64_t limb_transforms = 0;
+};
+
+static int rag_grid(bool fwd) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (fwd)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ragged_pass_kernel<true>, 256, kRagSmem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ragged_pass_kernel<false>, 256, kRagSmem);
+    return std::max(1, per) * std::max(1, sms);
+}
+
+// Enqueue one replay of the batch on `st`: re-arm the counters, then the two
+// persistent passes.
+static cudaError_t rag_enqueue(const hx_batch_s* b, cudaStream_t st, bool capturing) {
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const uint32_t ns[2] = {b->nA, b->nB};
+    for (int p = 0; p < 2; ++p) {
+        if (!ns[p]) continue;
+        const RagTile* t = b->d_tiles + (p ? b->nA : 0);
+        const unsigned grid = (unsigned)std::min<uint64_t>(ns[p], (uint64_t)b->grid);
+        if (b->forward)
+            ragged_pass_kernel<true><<<grid, 256, kRagSmem, st>>>(t, ns[p], b->d_counters + p);
+        else
+            ragged_pass_kernel<false><<<grid, 256, kRagSmem, st>>>(t, ns[p], b->d_counters + p);
+        if (!capturing) count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static void rag_free(hx_batch_s* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_counters);
+    delete b;
+}
+
+extern "C" int hx_batch_create(hx_batch_t* out, const hx_ragged_item* items, uint32_t n_items,
+                               uint32_t direction, uint32_t in_mf, uint32_t out_mf) {
+    if (!out || !items) return HX_ERR_NULL;
+    *out = nullptr;
+    if (n_items == 0 || (direction != 1 && direction != 2)) return HX_ERR_ARG;
+    const bool fwd = direction == 1;
+    if (fwd ? !(in_mf == 1 || in_mf == 2 || in_mf == 4) || !(out_mf == 1 || out_mf == 4)
+            : !(in_mf == 1 || in_mf == 2) || !(out_mf == 1 || out_mf == 2))
+        return HX_ERR_MOD_FACTOR;
+    std::vector<RagTile> A, B;
+    uint64_t lt = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const hx_ragged_item& it = items[i];
+        if (!it.plan || !it.d_in || !it.d_out) return HX_ERR_NULL;
+        if (((uintptr_t)it.d_in | (uintptr_t)it.d_out) & 15u) return HX_ERR_ALIGN;
+        if (it.n_polys == 0) return HX_ERR_ARG;
+        if (it.plan->device != dev) return HX_ERR_ARG;
+        const hx_plan_s* p = it.plan;
+        const uint64_t bytes = (uint64_t)it.n_polys * p->n_limbs * p->N * 8;
+        if (it.d_in != it.d_out && (uintptr_t)it.d_in < (uintptr_t)it.d_out + bytes &&
+            (uintptr_t)it.d_out < (uintptr_t)it.d_in + bytes)
+            return HX_ERR_OVERLAP;
+        int k1, k2;
+        rag_kinds(p->logN, &k1, &k2);
+        // forward: column/single pass first; inverse: row pass first
+        const int first = fwd || k2 < 0 ? k1 : k2, second = k2 < 0 ? -1 : (fwd ? k2 : k1);
+        const uint32_t tiles = p->logN <= 11 ? 1u : (1u << (p->logN - 11));
+        for (uint32_t poly = 0; poly < it.n_polys; ++poly) {
+            for (uint32_t l = 0; l < p->n_limbs; ++l) {
+                const uint64_t off = ((uint64_t)poly * p->n_limbs + l) << p->logN;
+                for (uint32_t t = 0; t < tiles; ++t) {
+                    RagTile a{it.d_in + off, it.d_out + off, p->d_limbs + l, t, (uint8_t)first,
+                              (uint8_t)p->logN, (uint8_t)(second < 0), (uint8_t)out_mf};
+                    A.push_back(a);
+                    if (second >= 0) {
+                        RagTile b2{it.d_out + off, it.d_out + off, p->d_limbs + l, t,
+                                   (uint8_t)second, (uint8_t)p->logN, 1, (uint8_t)out_mf};
+                        B.push_back(b2);
+                    }
+                }
+                ++lt;
+            }
+        }
+    }
+    if (A.size() + B.size() >= (1ull << 32)) return HX_ERR_ARG;
+    hx_batch_s* b = new (std::nothrow) hx_batch_s();
+    if (!b) return HX_ERR_NOMEM;
+    b->device = dev;
+    b->forward = fwd;
+    b->nA = (uint32_t)A.size();
+    b->nB = (uint32_t)B.size();
+    b->limb_transforms = lt;
+    b->grid = rag_grid(fwd);
+    if (cudaMalloc((void**)&b->d_tiles, (A.size() + B.size()) * sizeof(RagTile)) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_counters, 2 * sizeof(uint32_t)) != cudaSuccess) {
+        rag_free(b);
+        return HX_ERR_NOMEM;
+    }
+    if (cudaMemcpy(b->d_tiles, A.data(), A.size() * sizeof(RagTile), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        (B.size() && cudaMemcpy(b->d_tiles + A.size(), B.data(), B.size() * sizeof(RagTile),
+                                cudaMemcpyHostToDevice) != cudaSuccess)) {
+        rag_free(b);
+        return HX_ERR_CUDA;
+    }
+    // capture one replay into a graph on a private stream
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        rag_free(b);
+        return HX_ERR_CUDA;
+    }
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = rag_enqueue(b, cs, true);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        rag_free(b);
+        return HX_ERR_CUDA;
+    }
+    *out = b;
+    return HX_OK;
+}
+
+extern "C" int hx_batch_run(hx_batch_t b, hx_stream_t stream) {
+    if (!b) return HX_ERR_NULL;
+    if (cudaGraphLaunch(b->exec, (cudaStream_t)stream) != cudaSuccess) return HX_ERR_CUDA;
+    count_launch((b->nA ? 1 : 0) + (b->nB ? 1 : 0));
+    return HX_OK;
+}
+
+extern "C" int hx_batch_info(hx_batch_t b, uint64_t* limb_transforms, uint64_t* tiles,
+                             uint32_t* launches) {
+    if (!b) return HX_ERR_NULL;
+    if (limb_transforms) *limb_transforms = b->limb_transforms;
+    if (tiles) *tiles = (uint64_t)b->nA + b->nB;
+    if (launches) *launches = (b->nA ? 1 : 0) + (b->nB ? 1 : 0);
+    return HX_OK;
+}
+
+extern "C" int hx_batch_destroy(hx_batch_t b) {
+    if (!b) return HX_ERR_NULL;
+    rag_free(b);
+    return HX_OK;
+}

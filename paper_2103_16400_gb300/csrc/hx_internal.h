@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -35,6 +36,16 @@ struct NttCfg {
     PassCfg pass[2];
 };
 
+// Device twiddle tables of one (device, N, q, psi): fwd[N] then inv[N] pairs,
+// shared by every plan that uses them (plan.cpp keeps the cache).
+struct TableEntry {
+    int device = 0;
+    void* d_mem = nullptr;
+    size_t bytes = 0;
+    LimbDev ld{};            // constants with fwd/inv pointing into d_mem
+    ~TableEntry();
+};
+
 }  // namespace hx
 
 struct hx_plan_s {
@@ -43,7 +54,7 @@ struct hx_plan_s {
     uint32_t n_limbs = 0;
     int device = 0;
     std::vector<uint64_t> moduli, roots;
-    void* d_tables = nullptr;       // fwd then inv tables, all limbs
+    std::vector<std::shared_ptr<hx::TableEntry>> tables;   // one per limb (may repeat)
     hx::LimbDev* d_limbs = nullptr;
     std::vector<hx::LimbDev> h_limbs;
     uint64_t device_bytes = 0;
@@ -60,6 +71,9 @@ bool is_prime_u64(uint64_t n);
 uint64_t powmod_u64(uint64_t a, uint64_t e, uint64_t q);
 uint64_t min_primitive_root(uint64_t N, uint64_t q);
 NttCfg default_cfg(int logN, bool forward);
+int acquire_tables(int device, uint64_t N, int logN, const std::vector<uint64_t>& moduli,
+                   const std::vector<uint64_t>& roots,
+                   std::vector<std::shared_ptr<TableEntry>>* out);
 
 // ntt.cu
 cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,

@@ -275,6 +275,29 @@ __device__ __forceinline__ void ntt_rounds(uint64_t* sm, const ulonglong2* __res
     }
 }
 
+// One tile of one pass, by the whole block (TE >> LOG_R threads): stage in
+// through shared memory where the first round's map is strided, run the
+// rounds, stage out where the last round's map is strided.
+template <bool FWD, bool COLUMN, int LOG_R, int K>
+__device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, const LimbDev& lc,
+                                             uint32_t TE) {
+    constexpr bool staged_in = !COLUMN && !FWD;
+    constexpr bool staged_out = !COLUMN && FWD;
+    if (staged_in) {
+        tile_to_smem<K>(sm, c, TE);
+        __syncthreads();
+    }
+    const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
+    if (lc.narrow)
+        ntt_rounds<FWD, COLUMN, uint32_t, LOG_R, K, 0>(sm, tw, lc, c);
+    else
+        ntt_rounds<FWD, COLUMN, uint64_t, LOG_R, K, 0>(sm, tw, lc, c);
+    if (staged_out) {
+        __syncthreads();
+        smem_to_tile<K>(sm, c, TE);
+    }
+}
+
 template <bool FWD, bool COLUMN, int LOG_R, int K>
 __global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
     extern __shared__ uint64_t sm[];
@@ -298,22 +321,7 @@ __global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
     c.nthreads = TE >> LOG_R;
     c.out_mf = a.out_mf;
     c.last = a.last != 0;
-
-    constexpr bool staged_in = !COLUMN && !FWD;
-    constexpr bool staged_out = !COLUMN && FWD;
-    if (staged_in) {
-        tile_to_smem<K>(sm, c, TE);
-        __syncthreads();
-    }
-    const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
-    if (lc.narrow)
-        ntt_rounds<FWD, COLUMN, uint32_t, LOG_R, K, 0>(sm, tw, lc, c);
-    else
-        ntt_rounds<FWD, COLUMN, uint64_t, LOG_R, K, 0>(sm, tw, lc, c);
-    if (staged_out) {
-        __syncthreads();
-        smem_to_tile<K>(sm, c, TE);
-    }
+    process_tile<FWD, COLUMN, LOG_R, K>(sm, c, lc, TE);
 }
 
 // ---------------------------------------------------------------------------

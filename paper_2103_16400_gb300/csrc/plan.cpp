@@ -10,7 +10,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <thread>
+#include <tuple>
 
 #include "hx_internal.h"
 
@@ -132,6 +134,94 @@ NttCfg default_cfg(int logN, bool forward) {
     return c;
 }
 
+// ---------------------------------------------------------------- table cache
+// Twiddle tables depend only on (device, N, q, psi), so plans share them: a
+// process-wide map holds weak references, plans hold strong ones, and a table
+// is freed with the last plan that uses it.  Many plans over overlapping
+// prime sets (ragged batches, served requests) then cost one table per
+// distinct (N, q, psi).
+TableEntry::~TableEntry() {
+    if (!d_mem) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != device) cudaSetDevice(device);
+    cudaFree(d_mem);
+    if (prev != device) cudaSetDevice(prev);
+}
+
+namespace {
+typedef std::tuple<int, uint64_t, uint64_t, uint64_t> TableKey;
+std::mutex g_table_mu;
+std::map<TableKey, std::weak_ptr<TableEntry>> g_tables;
+}  // namespace
+
+int acquire_tables(int device, uint64_t N, int logN, const std::vector<uint64_t>& moduli,
+                   const std::vector<uint64_t>& roots,
+                   std::vector<std::shared_ptr<TableEntry>>* out) {
+    std::lock_guard<std::mutex> g(g_table_mu);
+    const size_t L = moduli.size();
+    out->assign(L, nullptr);
+    std::vector<size_t> missing;
+    std::map<TableKey, size_t> first_of;   // duplicates within one plan share one fill
+    for (size_t l = 0; l < L; ++l) {
+        const TableKey key(device, N, moduli[l], roots[l]);
+        auto it = g_tables.find(key);
+        if (it != g_tables.end()) (*out)[l] = it->second.lock();
+        if (!(*out)[l] && !first_of.count(key)) {
+            first_of[key] = l;
+            missing.push_back(l);
+        }
+    }
+    // fill the new tables on the host in parallel, then upload each
+    std::vector<std::vector<ulonglong2>> host(missing.size());
+    std::vector<LimbDev> lds(missing.size());
+    unsigned nthreads = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
+    nthreads = std::min<unsigned>(nthreads, (unsigned)std::max<size_t>(missing.size(), 1));
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nthreads; ++t) {
+        pool.emplace_back([&, t]() {
+            for (size_t m = t; m < missing.size(); m += nthreads) {
+                const size_t l = missing[m];
+                host[m].resize(2 * N);
+                fill_limb(N, logN, moduli[l], roots[l], host[m].data(), host[m].data() + N, &lds[m]);
+            }
+        });
+    }
+    for (auto& th : pool) th.join();
+    for (size_t m = 0; m < missing.size(); ++m) {
+        const size_t l = missing[m];
+        auto e = std::make_shared<TableEntry>();
+        e->device = device;
+        e->bytes = 2 * N * sizeof(ulonglong2);
+        if (cudaMalloc(&e->d_mem, e->bytes) != cudaSuccess) {
+            e->d_mem = nullptr;
+            out->clear();
+            return HX_ERR_NOMEM;
+        }
+        if (cudaMemcpy(e->d_mem, host[m].data(), e->bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            out->clear();
+            return HX_ERR_CUDA;
+        }
+        e->ld = lds[m];
+        e->ld.fwd = (const ulonglong2*)e->d_mem;
+        e->ld.inv = (const ulonglong2*)e->d_mem + N;
+        const TableKey key(device, N, moduli[l], roots[l]);
+        g_tables[key] = e;
+        (*out)[l] = e;
+    }
+    for (size_t l = 0; l < L; ++l) {
+        if (!(*out)[l]) (*out)[l] = g_tables[TableKey(device, N, moduli[l], roots[l])].lock();
+    }
+    // forget expired entries
+    for (auto it = g_tables.begin(); it != g_tables.end();) {
+        if (it->second.expired())
+            it = g_tables.erase(it);
+        else
+            ++it;
+    }
+    return HX_OK;
+}
+
 }  // namespace hx
 
 using namespace hx;
@@ -168,49 +258,31 @@ extern "C" int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_modu
     p->cfg_fwd = default_cfg(logN, true);
     p->cfg_inv = default_cfg(logN, false);
     cudaGetDevice(&p->device);
-
-    const size_t table_pairs = (size_t)N * n_limbs;
-    std::vector<ulonglong2> hf(table_pairs), hi(table_pairs);
+    int st = acquire_tables(p->device, N, logN, p->moduli, roots, &p->tables);
+    if (st != HX_OK) {
+        delete p;
+        return st;
+    }
     p->h_limbs.resize(n_limbs);
-    unsigned nthreads = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
-    nthreads = std::min<unsigned>(nthreads, n_limbs);
-    std::vector<std::thread> pool;
-    for (unsigned t = 0; t < nthreads; ++t) {
-        pool.emplace_back([&, t]() {
-            for (uint32_t l = t; l < n_limbs; l += nthreads)
-                fill_limb(N, logN, p->moduli[l], roots[l], &hf[(size_t)l * N], &hi[(size_t)l * N],
-                          &p->h_limbs[l]);
-        });
-    }
-    for (auto& th : pool) th.join();
-
-    const size_t tbytes = table_pairs * sizeof(ulonglong2);
-    if (cudaMalloc(&p->d_tables, 2 * tbytes) != cudaSuccess) {
-        delete p;
-        return HX_ERR_NOMEM;
-    }
+    for (uint32_t l = 0; l < n_limbs; ++l) p->h_limbs[l] = p->tables[l]->ld;
     if (cudaMalloc((void**)&p->d_limbs, n_limbs * sizeof(LimbDev)) != cudaSuccess) {
-        cudaFree(p->d_tables);
         delete p;
         return HX_ERR_NOMEM;
     }
-    ulonglong2* dfwd = (ulonglong2*)p->d_tables;
-    ulonglong2* dinv = dfwd + table_pairs;
-    for (uint32_t l = 0; l < n_limbs; ++l) {
-        p->h_limbs[l].fwd = dfwd + (size_t)l * N;
-        p->h_limbs[l].inv = dinv + (size_t)l * N;
-    }
-    cudaError_t e1 = cudaMemcpy(dfwd, hf.data(), tbytes, cudaMemcpyHostToDevice);
-    cudaError_t e2 = cudaMemcpy(dinv, hi.data(), tbytes, cudaMemcpyHostToDevice);
-    cudaError_t e3 = cudaMemcpy(p->d_limbs, p->h_limbs.data(), n_limbs * sizeof(LimbDev),
-                                cudaMemcpyHostToDevice);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-        cudaFree(p->d_tables);
+    if (cudaMemcpy(p->d_limbs, p->h_limbs.data(), n_limbs * sizeof(LimbDev),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(p->d_limbs);
         delete p;
         return HX_ERR_CUDA;
     }
-    p->device_bytes = 2 * tbytes + n_limbs * sizeof(LimbDev);
+    p->device_bytes = n_limbs * sizeof(LimbDev);
+    std::vector<const TableEntry*> seen;
+    for (auto& t : p->tables) {
+        if (std::find(seen.begin(), seen.end(), t.get()) == seen.end()) {
+            seen.push_back(t.get());
+            p->device_bytes += t->bytes;
+        }
+    }
     *out = p;
     return HX_OK;
 }
@@ -220,8 +292,8 @@ extern "C" int hx_plan_destroy(hx_plan_t p) {
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != p->device) cudaSetDevice(p->device);
-    cudaFree(p->d_tables);
     cudaFree(p->d_limbs);
+    p->tables.clear();   // drops this plan's references; unused tables are freed
     if (prev != p->device) cudaSetDevice(prev);
     delete p;
     return HX_OK;
