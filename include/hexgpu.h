@@ -65,7 +65,8 @@ typedef enum hx_status {
     HX_ERR_ARG = -8,          /* another argument is out of range */
     HX_ERR_OVERLAP = -9,      /* result and operand partially overlap */
     HX_ERR_TIMEOUT = -10,     /* a device-side wait gave up */
-    HX_ERR_NOMEM = -11        /* device or host allocation failed */
+    HX_ERR_NOMEM = -11,       /* device or host allocation failed */
+    HX_ERR_CAPACITY = -12     /* request exceeds a fixed scratch capacity */
 } hx_status;
 
 const char* hx_strerror(int status);
@@ -270,6 +271,33 @@ int hx_batch_run(hx_batch_t batch, hx_stream_t stream);
 int hx_batch_info(hx_batch_t batch, uint64_t* limb_transforms, uint64_t* tiles,
                   uint32_t* launches);
 int hx_batch_destroy(hx_batch_t batch);
+
+/* hx_batch_run_static: runs the same ragged set of transforms once, like
+ * hx_batch_create + hx_batch_run + hx_batch_destroy, but without allocating
+ * any device memory.  The paper has no counterpart; it exists for callers
+ * that cannot call cudaMalloc where they need the transforms -- a serving
+ * loop that admits work against a fixed device-memory budget, an application
+ * whose own memory pool owns the whole GPU, or a latency-critical path that
+ * cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * The work counters and the tile list live in one fixed 4 MiB array compiled
+ * into the library; every GPU that loads the library holds that array until
+ * the process exits.  A request may hold at most 131064 tiles (one tile per
+ * 2048 coefficients per pass: N <= 2^11 takes one pass, larger N two);
+ * larger requests are refused with HX_ERR_CAPACITY before anything is
+ * enqueued.  Arguments, semantics and the other errors are those of
+ * hx_batch_create; the tile list is copied from host memory on `stream`
+ * and the kernels are enqueued there (no graph).
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
+ * call's contents (the counters are re-zeroed on `stream` by each call):
+ * calls whose work overlaps on the GPU -- on different streams, or on one
+ * device from several host threads without ordering -- race on it. */
+int hx_batch_run_static(const hx_ragged_item* h_items, uint32_t n_items, uint32_t direction,
+                        uint32_t input_mod_factor, uint32_t output_mod_factor,
+                        hx_stream_t stream);
 
 /* ---------------------------------------------------------------- measurement
  * Support for the benchmark; the paper has no counterpart.

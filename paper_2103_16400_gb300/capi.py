@@ -46,6 +46,7 @@ _SIGS = {
     "hx_batch_run": [VP, VP],
     "hx_batch_info": [VP, P64, P64, ctypes.POINTER(U32)],
     "hx_batch_destroy": [VP],
+    "hx_batch_run_static": [VP, U32, U32, U32, U32, VP],
     "hx_launch_count": [],
     "hx_probe_int_mul_rate": [U32, U32, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_float), VP],
@@ -177,6 +178,18 @@ class RaggedItem(ctypes.Structure):
     """hx_ragged_item: polynomials sharing one plan, in a ragged batch."""
     _fields_ = [("plan", VP), ("d_in", VP), ("d_out", VP), ("n_polys", U32),
                 ("reserved", U32)]
+
+
+def hx_batch_run_static(items, direction: int = 1, input_mod_factor: int = 1,
+                        output_mod_factor: int = 1, stream=None):
+    """One run of a ragged set of transforms with no device allocation (the
+    library's fixed scratch array holds the work list); items as for Batch."""
+    items = list(items)
+    arr = (RaggedItem * len(items))(*[RaggedItem(_h(p), ptr(i), ptr(o), n, 0)
+                                      for p, i, o, n in items])
+    _check("hx_batch_run_static", load().hx_batch_run_static(
+        ctypes.cast(arr, VP), len(items), direction, input_mod_factor, output_mod_factor,
+        _stream(stream)))
 
 
 class Batch:

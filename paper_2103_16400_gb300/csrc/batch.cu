@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ntt_kernels.cuh"
@@ -269,5 +270,133 @@ extern "C" int hx_batch_info(hx_batch_t b, uint64_t* limb_transforms, uint64_t* 
 extern "C" int hx_batch_destroy(hx_batch_t b) {
     if (!b) return HX_ERR_NULL;
     rag_free(b);
+    return HX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One-shot ragged run for callers that must not allocate device memory.
+//
+// hx_batch_create allocates its tile list and work counters with cudaMalloc.
+// Some callers cannot do that at the point of use: a serving loop that admits
+// work against a fixed device-memory budget, an application whose own memory
+// pool owns the whole GPU, or a latency-critical path that cannot afford the
+// device-wide synchronisation cudaMalloc and cudaFree imply.  For them this
+// entry point keeps the counters and the tile list in a fixed array compiled
+// into the library (kStaticScratchBytes per GPU that loads it, held until the
+// process exits), and calls no cudaMalloc, cudaFree or other allocating
+// device routine.
+// ---------------------------------------------------------------------------
+namespace hx {
+
+constexpr size_t kStaticScratchBytes = 4u << 20;          // 4 MiB per device
+constexpr size_t kStaticHeader = 256;                      // the two counters
+constexpr uint32_t kStaticMaxTiles =
+    (uint32_t)((kStaticScratchBytes - kStaticHeader) / sizeof(RagTile));   // 131064
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// The host-side name of g_static_scratch is only a stand-in, not a device
+// address; the address is fetched once per device, with that device current.
+static std::mutex g_static_mu;
+static void* g_static_addr[128];
+
+static int static_scratch_address(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HX_ERR_CUDA;
+    if (dev < 0 || dev >= 128) return HX_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return HX_ERR_CUDA;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return HX_OK;
+}
+
+}  // namespace hx
+
+extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items,
+                                   uint32_t direction, uint32_t in_mf, uint32_t out_mf,
+                                   hx_stream_t stream) {
+    if (!items) return HX_ERR_NULL;
+    if (n_items == 0 || (direction != 1 && direction != 2)) return HX_ERR_ARG;
+    const bool fwd = direction == 1;
+    if (fwd ? !(in_mf == 1 || in_mf == 2 || in_mf == 4) || !(out_mf == 1 || out_mf == 4)
+            : !(in_mf == 1 || in_mf == 2) || !(out_mf == 1 || out_mf == 2))
+        return HX_ERR_MOD_FACTOR;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // count the tiles first, so an oversized request is refused before any work
+    uint64_t n_first = 0, n_second = 0;
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const hx_ragged_item& it = items[i];
+        if (!it.plan || !it.d_in || !it.d_out) return HX_ERR_NULL;
+        if (((uintptr_t)it.d_in | (uintptr_t)it.d_out) & 15u) return HX_ERR_ALIGN;
+        if (it.n_polys == 0 || it.plan->device != dev) return HX_ERR_ARG;
+        const hx_plan_s* p = it.plan;
+        const uint64_t bytes = (uint64_t)it.n_polys * p->n_limbs * p->N * 8;
+        if (it.d_in != it.d_out && (uintptr_t)it.d_in < (uintptr_t)it.d_out + bytes &&
+            (uintptr_t)it.d_out < (uintptr_t)it.d_in + bytes)
+            return HX_ERR_OVERLAP;
+        const uint64_t tiles = p->logN <= 11 ? 1u : (1u << (p->logN - 11));
+        const uint64_t t = tiles * it.n_polys * p->n_limbs;
+        n_first += t;
+        if (p->logN > 11) n_second += t;
+    }
+    if (n_first + n_second > kStaticMaxTiles) return HX_ERR_CAPACITY;
+
+    std::vector<RagTile> tiles;   // host staging of the tile list (first pass, then second)
+    tiles.reserve(n_first + n_second);
+    for (int pass = 0; pass < 2; ++pass) {
+        for (uint32_t i = 0; i < n_items; ++i) {
+            const hx_ragged_item& it = items[i];
+            const hx_plan_s* p = it.plan;
+            int k1, k2;
+            rag_kinds(p->logN, &k1, &k2);
+            if (pass == 1 && k2 < 0) continue;
+            const int first = fwd || k2 < 0 ? k1 : k2, second = fwd ? k2 : k1;
+            const uint32_t nt = p->logN <= 11 ? 1u : (1u << (p->logN - 11));
+            for (uint32_t poly = 0; poly < it.n_polys; ++poly) {
+                for (uint32_t l = 0; l < p->n_limbs; ++l) {
+                    const uint64_t off = ((uint64_t)poly * p->n_limbs + l) << p->logN;
+                    for (uint32_t t = 0; t < nt; ++t) {
+                        if (pass == 0)
+                            tiles.push_back(RagTile{it.d_in + off, it.d_out + off, p->d_limbs + l, t,
+                                                    (uint8_t)first, (uint8_t)p->logN,
+                                                    (uint8_t)(k2 < 0), (uint8_t)out_mf});
+                        else
+                            tiles.push_back(RagTile{it.d_out + off, it.d_out + off, p->d_limbs + l,
+                                                    t, (uint8_t)second, (uint8_t)p->logN, 1,
+                                                    (uint8_t)out_mf});
+                    }
+                }
+            }
+        }
+    }
+    void* base = nullptr;
+    int st = static_scratch_address(&base);
+    if (st != HX_OK) return st;
+    uint32_t* counters = (uint32_t*)base;
+    RagTile* d_tiles = (RagTile*)((unsigned char*)base + kStaticHeader);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: re-zero the counters
+    if (cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return HX_ERR_CUDA;
+    if (cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(RagTile),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return HX_ERR_CUDA;
+    const int grid = rag_grid(fwd);
+    const uint32_t ns[2] = {(uint32_t)n_first, (uint32_t)n_second};
+    for (int p = 0; p < 2; ++p) {
+        if (!ns[p]) continue;
+        const RagTile* t = d_tiles + (p ? n_first : 0);
+        const unsigned g = (unsigned)std::min<uint64_t>(ns[p], (uint64_t)grid);
+        if (fwd)
+            ragged_pass_kernel<true><<<g, 256, kRagSmem, s>>>(t, ns[p], counters + p);
+        else
+            ragged_pass_kernel<false><<<g, 256, kRagSmem, s>>>(t, ns[p], counters + p);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) return HX_ERR_CUDA;
+    }
     return HX_OK;
 }

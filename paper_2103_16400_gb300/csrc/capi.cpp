@@ -106,6 +106,7 @@ const char* hx_strerror(int s) {
         case HX_ERR_OVERLAP: return "result and operand partially overlap";
         case HX_ERR_TIMEOUT: return "device-side wait timed out";
         case HX_ERR_NOMEM: return "allocation failed";
+        case HX_ERR_CAPACITY: return "request exceeds the fixed scratch capacity";
         default: return "unknown status";
     }
 }
