@@ -179,6 +179,85 @@ def ragged_report(torch, n_polys=512, reps=5):
             "speedup_vs_per_limb": t_limb / t_batch, "bit_exact_equal": bool(same)}
 
 
+# ------------------------------------------------------------------ serving
+def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30):
+    """Poisson arrivals of polynomial-multiply requests (N uniform over
+    {2^12, 2^14, 2^16}, 4-32 limbs of the mixed 30/50/60-bit basis, operands
+    uniform mod q and resident in HBM) at each rate: the continuous-batching
+    server against the same requests served one by one with plain calls.
+    Reports throughput and p50/p99 latency and checks every result is the
+    same bits both ways."""
+    from paper_2103_16400_gb300 import serve
+    from paper_2103_16400_gb300.tensors import to_device
+    moduli = W.mixed_width_primes(32)
+    Ns = (1 << 12, 1 << 14, 1 << 16)
+    pool = {N: [(to_device(W.poly_batch(W.SEED_BASE + 5, 10 * k, 1, moduli, N)[0]),
+                 to_device(W.poly_batch(W.SEED_BASE + 5, 10 * k + 1, 1, moduli, N)[0]))
+                for k in range(4)] for N in Ns}
+    draws = W.splitmix64_block(W.stream_key(W.SEED_BASE + 5, 1), 0, 4 * n_req)
+    spec = [(Ns[int(draws[3 * i] % np.uint64(3))], 4 + int(draws[3 * i + 1] % np.uint64(29)),
+             int(draws[3 * i + 2] % np.uint64(4))) for i in range(n_req)]
+    u = (W.splitmix64_block(W.stream_key(W.SEED_BASE + 5, 2), 0, n_req) >> np.uint64(11)) \
+        .astype(np.float64) / float(1 << 53)
+
+    def requests():
+        return [serve.Request(N, tuple(moduli[:L]), pool[N][k][0][:L], pool[N][k][1][:L])
+                for N, L, k in spec]
+
+    srv = serve.Server(hbm_budget=budget, streams=3)
+    for N in Ns:                                   # plans (twiddles) resident up front
+        for L in range(4, 33):
+            srv.plan(N, moduli[:L])
+    plans = dict(srv.plans)
+    # warm both paths (torch allocator, pinned pools, kernels)
+    warm = requests()[:64]
+    with srv:
+        for f in [srv.submit(r) for r in warm]:
+            f.result()
+    srv = serve.Server(hbm_budget=budget, streams=3)
+    srv.plans = plans
+    serve.serve_one_by_one(requests()[:64], plans=plans)
+    torch.cuda.synchronize()
+
+    lt_per_req = [3 * L for _, L, _ in spec]
+    out = []
+    for rate in rates:
+        arrivals = np.cumsum(-np.log1p(-u) / rate)
+        served = requests()
+        srv = serve.Server(hbm_budget=budget, streams=3)
+        srv.plans = plans
+        srv.start()
+        t0 = time.perf_counter()
+        futs = []
+        for r, t in zip(served, arrivals):
+            while True:                  # wait for the arrival without holding the GIL
+                wait = t - (time.perf_counter() - t0)
+                if wait <= 0:
+                    break
+                time.sleep(wait if wait > 2e-4 else 0)
+            futs.append(srv.submit(r))
+        for f in futs:
+            f.result(timeout=600)
+        srv.stop()
+        base = requests()
+        serve.serve_one_by_one(base, arrivals, plans=plans)
+        same = all(torch.equal(a.result, b.result) for a, b in zip(served, base))
+
+        def summary(rs):
+            lat = np.array([r.latency for r in rs]) * 1e3
+            span = max(r.done for r in rs) - min(r.arrival for r in rs)
+            return {"requests_per_s": len(rs) / span,
+                    "limb_transforms_per_s": sum(lt_per_req) / span,
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "mean_ms": float(lat.mean())}
+        out.append({"offered_rate_per_s": rate, "requests": n_req, "served": summary(served),
+                    "one_by_one": summary(base), "batches": srv.stats["batches"],
+                    "max_batch": srv.stats["max_batch"], "bit_exact_equal": bool(same)})
+    return {"workload": "poly-multiply requests, N in {2^12,2^14,2^16}, 4-32 limbs, "
+                        "operands HBM-resident, Poisson arrivals", "hbm_budget_bytes": budget,
+            "streams": 3, "rates": out}
+
+
 # ------------------------------------------------------------------ clocks
 _REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
             0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
@@ -405,6 +484,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ragged", action="store_true",
                     help="skip the ragged-batch report (512 polynomials, mixed N)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving report (Poisson arrivals, p50/p99 latency)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--case", default="pipeline",
                     choices=["pipeline", "fwd", "inv", "tensor", "probes"],
@@ -532,6 +613,8 @@ def main():
             "clocks": clocks.summary()}
     if not args.no_ragged:
         line["batched"] = ragged_report(torch)
+    if not args.no_serving:
+        line["serving"] = serving_report(torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(N, wl.moduli, s, sets)
     if rank == 0:

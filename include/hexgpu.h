@@ -299,6 +299,38 @@ int hx_batch_run_static(const hx_ragged_item* h_items, uint32_t n_items, uint32_
                         uint32_t input_mod_factor, uint32_t output_mod_factor,
                         hx_stream_t stream);
 
+/* --------------------------------------------- ragged products (serving primitive)
+ * hx_polymul_ragged: for every item, d_result = d_a * d_b in R_q for each
+ *   polynomial and limb of the item's plan, composed as the paper's Listing 4
+ *   (forward NTT of both operands with output range [0, 4q), EltwiseMultMod
+ *   with input_mod_factor 4, inverse NTT to [0, q)).  Items may differ in N
+ *   and moduli (every modulus below 2^61).  Operands are read, never
+ *   written: the forward transforms go out of place into the workspace and
+ *   the inverse writes the result.  The whole set runs as five kernels on
+ *   `stream` (two forward passes, one product, two inverse passes).
+ *   hx_polymul_item: plan; d_a, d_b, d_result: device [n_polys][limbs][N]
+ *   (d_result may equal d_a or d_b); n_polys >= 1.
+ *   d_workspace: caller-owned device memory, 256-byte aligned, at least the
+ *   size hx_polymul_ragged_workspace reports (twice the operand size plus
+ *   32 bytes per tile); it holds the spectra, the tile lists and the work
+ *   counters, so the library allocates nothing.  A workspace may be reused
+ *   by calls ordered on one stream, not by concurrent ones.
+ *   Errors: HX_ERR_NULL, HX_ERR_ALIGN, HX_ERR_ARG, HX_ERR_MODULUS,
+ *   HX_ERR_CAPACITY (workspace too small), HX_ERR_CUDA. */
+typedef struct hx_polymul_item {
+    hx_plan_t plan;
+    const uint64_t* d_a;
+    const uint64_t* d_b;
+    uint64_t* d_result;
+    uint32_t n_polys;
+    uint32_t reserved;
+} hx_polymul_item;
+
+int hx_polymul_ragged_workspace(const hx_polymul_item* h_items, uint32_t n_items,
+                                uint64_t* bytes);
+int hx_polymul_ragged(const hx_polymul_item* h_items, uint32_t n_items, void* d_workspace,
+                      uint64_t workspace_bytes, hx_stream_t stream);
+
 /* ---------------------------------------------------------------- measurement
  * Support for the benchmark; the paper has no counterpart.
  *

@@ -47,6 +47,8 @@ _SIGS = {
     "hx_batch_info": [VP, P64, P64, ctypes.POINTER(U32)],
     "hx_batch_destroy": [VP],
     "hx_batch_run_static": [VP, U32, U32, U32, U32, VP],
+    "hx_polymul_ragged_workspace": [VP, U32, P64],
+    "hx_polymul_ragged": [VP, U32, VP, U64, VP],
     "hx_launch_count": [],
     "hx_probe_int_mul_rate": [U32, U32, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_float), VP],
@@ -178,6 +180,34 @@ class RaggedItem(ctypes.Structure):
     """hx_ragged_item: polynomials sharing one plan, in a ragged batch."""
     _fields_ = [("plan", VP), ("d_in", VP), ("d_out", VP), ("n_polys", U32),
                 ("reserved", U32)]
+
+
+class PolymulItem(ctypes.Structure):
+    """hx_polymul_item: products a * b of polynomials sharing one plan."""
+    _fields_ = [("plan", VP), ("d_a", VP), ("d_b", VP), ("d_result", VP), ("n_polys", U32),
+                ("reserved", U32)]
+
+
+def polymul_items(items):
+    """ctypes array of PolymulItem from (plan, a, b, result, n_polys) tuples."""
+    items = list(items)
+    return (PolymulItem * len(items))(*[PolymulItem(_h(p), ptr(a), ptr(b), ptr(r), n, 0)
+                                        for p, a, b, r, n in items]), len(items)
+
+
+def hx_polymul_ragged_workspace(items) -> int:
+    arr, n = items if isinstance(items, tuple) else polymul_items(items)
+    out = U64()
+    _check("hx_polymul_ragged_workspace", load().hx_polymul_ragged_workspace(
+        ctypes.cast(arr, VP), n, ctypes.byref(out)))
+    return out.value
+
+
+def hx_polymul_ragged(items, workspace, workspace_bytes: int, stream=None):
+    """items: (plan, a, b, result, n_polys) tuples or a polymul_items() pair."""
+    arr, n = items if isinstance(items, tuple) else polymul_items(items)
+    _check("hx_polymul_ragged", load().hx_polymul_ragged(
+        ctypes.cast(arr, VP), n, ptr(workspace), workspace_bytes, _stream(stream)))
 
 
 def hx_batch_run_static(items, direction: int = 1, input_mod_factor: int = 1,

@@ -400,3 +400,176 @@ extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items
     }
     return HX_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Ragged polynomial products in a caller-provided workspace (the serving
+// primitive).  For every item, c = a * b in R_q per the paper's Listing 4:
+// forward NTTs of a and b written out of place into the workspace (outputs
+// in [0, 4q)), the element-wise product with input_mod_factor 4, and the
+// inverse NTT written straight into the result.  Items may differ in N and
+// moduli; the whole set is five kernel launches (two forward passes, one
+// product, two inverse passes).  The workspace holds the spectra, the tile
+// lists and the work counters, so the library allocates nothing.
+// ---------------------------------------------------------------------------
+namespace hx {
+
+struct MulTile {   // a[i] <- a[i] * b[i] mod q for i < count (count even)
+    uint64_t* a;
+    const uint64_t* b;
+    const LimbDev* lc;
+    uint32_t count;
+    uint32_t pad;
+};
+static_assert(sizeof(MulTile) == 32, "descriptor is 32 bytes");
+
+__global__ void __launch_bounds__(256) mul_tiles_kernel(const MulTile* __restrict__ tiles) {
+    const MulTile d = tiles[blockIdx.x];
+    const uint64_t q = d.lc->q;
+    const Barrett br{q, d.lc->barrett_k, d.lc->barrett_qm1};
+    ulonglong2* A = reinterpret_cast<ulonglong2*>(d.a);
+    const ulonglong2* B = reinterpret_cast<const ulonglong2*>(d.b);
+    for (uint32_t i = threadIdx.x; i < d.count / 2; i += blockDim.x) {
+        ulonglong2 x = A[i];
+        const ulonglong2 y = B[i];
+        x.x = barrett_mulmod(small_mod<4>(x.x, q), small_mod<4>(y.x, q), br);
+        x.y = barrett_mulmod(small_mod<4>(x.y, q), small_mod<4>(y.y, q), br);
+        A[i] = x;
+    }
+}
+
+struct PolymulLayout {
+    uint64_t spectra = 0;      // bytes of A and B slots
+    uint64_t fA = 0, fB = 0, iA = 0, iB = 0, mul = 0;   // descriptor counts
+    uint64_t tiles_off = 0, total = 0;
+};
+
+static int polymul_layout(const hx_polymul_item* items, uint32_t n, PolymulLayout* L) {
+    *L = PolymulLayout();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (uint32_t i = 0; i < n; ++i) {
+        const hx_polymul_item& it = items[i];
+        if (!it.plan || !it.d_a || !it.d_b || !it.d_result) return HX_ERR_NULL;
+        if (((uintptr_t)it.d_a | (uintptr_t)it.d_b | (uintptr_t)it.d_result) & 15u)
+            return HX_ERR_ALIGN;
+        if (it.n_polys == 0 || it.plan->device != dev) return HX_ERR_ARG;
+        const hx_plan_s* p = it.plan;
+        for (uint64_t q : p->moduli)
+            if (q >= (1ull << 61)) return HX_ERR_MODULUS;     // 4q < 2^63 for the product
+        const uint64_t transforms = (uint64_t)it.n_polys * p->n_limbs;
+        const uint64_t tiles = p->logN <= 11 ? 1u : (1u << (p->logN - 11));
+        L->spectra += 2 * transforms * p->N * 8;
+        L->fA += 2 * transforms * tiles;
+        L->iA += transforms * tiles;
+        if (p->logN > 11) {
+            L->fB += 2 * transforms * tiles;
+            L->iB += transforms * tiles;
+        }
+        L->mul += transforms * std::max<uint64_t>(1, p->N / 2048);
+    }
+    L->tiles_off = 256 + L->spectra;
+    L->total = L->tiles_off + (L->fA + L->fB + L->iA + L->iB) * sizeof(RagTile) +
+               L->mul * sizeof(MulTile);
+    if (L->fA + L->fB >= (1ull << 32) || L->mul >= (1ull << 31)) return HX_ERR_ARG;
+    return HX_OK;
+}
+
+}  // namespace hx
+
+extern "C" int hx_polymul_ragged_workspace(const hx_polymul_item* items, uint32_t n_items,
+                                           uint64_t* bytes) {
+    if (!items || !bytes) return HX_ERR_NULL;
+    if (n_items == 0) return HX_ERR_ARG;
+    PolymulLayout L;
+    int st = polymul_layout(items, n_items, &L);
+    if (st != HX_OK) return st;
+    *bytes = L.total;
+    return HX_OK;
+}
+
+extern "C" int hx_polymul_ragged(const hx_polymul_item* items, uint32_t n_items, void* d_workspace,
+                                 uint64_t workspace_bytes, hx_stream_t stream) {
+    if (!items || !d_workspace) return HX_ERR_NULL;
+    if (n_items == 0) return HX_ERR_ARG;
+    if ((uintptr_t)d_workspace & 255u) return HX_ERR_ALIGN;
+    PolymulLayout L;
+    int st = polymul_layout(items, n_items, &L);
+    if (st != HX_OK) return st;
+    if (workspace_bytes < L.total) return HX_ERR_CAPACITY;
+    unsigned char* ws = (unsigned char*)d_workspace;
+    uint32_t* counters = (uint32_t*)ws;
+    // descriptors, in launch order: fwd A, fwd B, inv A, inv B, then products
+    std::vector<unsigned char> host((L.fA + L.fB + L.iA + L.iB) * sizeof(RagTile) +
+                                    L.mul * sizeof(MulTile));
+    RagTile* fA = (RagTile*)host.data();
+    RagTile* fB = fA + L.fA;
+    RagTile* iA = fB + L.fB;
+    RagTile* iB = iA + L.iA;
+    MulTile* mt = (MulTile*)(iB + L.iB);
+    uint64_t nfA = 0, nfB = 0, niA = 0, niB = 0, nm = 0;
+    uint64_t* spec = (uint64_t*)(ws + 256);
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const hx_polymul_item& it = items[i];
+        const hx_plan_s* p = it.plan;
+        int k1, k2;
+        rag_kinds(p->logN, &k1, &k2);
+        const uint64_t words = (uint64_t)it.n_polys * p->n_limbs << p->logN;
+        uint64_t* A = spec;
+        uint64_t* B = spec + words;
+        spec += 2 * words;
+        const uint32_t nt = p->logN <= 11 ? 1u : (1u << (p->logN - 11));
+        for (uint32_t poly = 0; poly < it.n_polys; ++poly) {
+            for (uint32_t l = 0; l < p->n_limbs; ++l) {
+                const uint64_t off = ((uint64_t)poly * p->n_limbs + l) << p->logN;
+                const LimbDev* lc = p->d_limbs + l;
+                const uint8_t lg = (uint8_t)p->logN, single = (uint8_t)(k2 < 0);
+                for (uint32_t t = 0; t < nt; ++t) {
+                    // forward: a -> A, b -> B (column/single pass first), out range [0, 4q)
+                    fA[nfA++] = RagTile{it.d_a + off, A + off, lc, t, (uint8_t)k1, lg, single, 4};
+                    fA[nfA++] = RagTile{it.d_b + off, B + off, lc, t, (uint8_t)k1, lg, single, 4};
+                    if (!single) {
+                        fB[nfB++] = RagTile{A + off, A + off, lc, t, (uint8_t)k2, lg, 1, 4};
+                        fB[nfB++] = RagTile{B + off, B + off, lc, t, (uint8_t)k2, lg, 1, 4};
+                    }
+                    // inverse: A -> result (row/single pass first), out range [0, q)
+                    iA[niA++] = RagTile{A + off, it.d_result + off, lc, t,
+                                        (uint8_t)(single ? k1 : k2), lg, single, 1};
+                    if (!single)
+                        iB[niB++] = RagTile{it.d_result + off, it.d_result + off, lc, t,
+                                            (uint8_t)k1, lg, 1, 1};
+                }
+                const uint32_t chunk = (uint32_t)std::min<uint64_t>(p->N, 2048);
+                for (uint64_t c = 0; c < p->N; c += chunk)
+                    mt[nm++] = MulTile{A + off + c, B + off + c, lc, chunk, 0};
+            }
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(counters, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return HX_ERR_CUDA;
+    if (cudaMemcpyAsync(ws + L.tiles_off, host.data(), host.size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return HX_ERR_CUDA;
+    const RagTile* dt = (const RagTile*)(ws + L.tiles_off);
+    const int gf = rag_grid(true), gi = rag_grid(false);
+    auto pass = [&](bool fwd, const RagTile* t, uint64_t cnt, uint32_t* ctr, int grid) {
+        if (!cnt) return cudaSuccess;
+        const unsigned g = (unsigned)std::min<uint64_t>(cnt, (uint64_t)grid);
+        if (fwd)
+            ragged_pass_kernel<true><<<g, 256, kRagSmem, s>>>(t, (uint32_t)cnt, ctr);
+        else
+            ragged_pass_kernel<false><<<g, 256, kRagSmem, s>>>(t, (uint32_t)cnt, ctr);
+        count_launch();
+        return cudaGetLastError();
+    };
+    cudaError_t e = pass(true, dt, L.fA, counters, gf);
+    if (e == cudaSuccess) e = pass(true, dt + L.fA, L.fB, counters + 1, gf);
+    if (e == cudaSuccess) {
+        const MulTile* dm = (const MulTile*)(dt + L.fA + L.fB + L.iA + L.iB);
+        mul_tiles_kernel<<<(unsigned)L.mul, 256, 0, s>>>(dm);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = pass(false, dt + L.fA + L.fB, L.iA, counters + 2, gi);
+    if (e == cudaSuccess) e = pass(false, dt + L.fA + L.fB + L.iA, L.iB, counters + 3, gi);
+    return e == cudaSuccess ? HX_OK : HX_ERR_CUDA;
+}

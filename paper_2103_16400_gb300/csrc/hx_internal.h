@@ -20,7 +20,8 @@ struct LimbDev {
     uint64_t ninv, ninv_p;      // N^-1 and its Shoup factor
     uint64_t ninv_w, ninv_w_p;  // N^-1 * psi^-brv(1) and its Shoup factor
     uint32_t narrow;            // 1: q < 2^30, 32-bit words, beta = 2^32
-    uint32_t pad;
+    uint32_t barrett_qm1;       // bitlen(q) - 1 (Barrett shift)
+    uint64_t barrett_k;         // floor(2^(63 + bitlen(q)) / q)
 };
 
 // One pass of a transform: CT stages [s0, s0 + K) on tiles of

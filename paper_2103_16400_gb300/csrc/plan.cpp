@@ -112,7 +112,10 @@ static void fill_limb(uint64_t N, int logN, uint64_t q, uint64_t psi, ulonglong2
     ld->ninv_w = ninv_w;
     ld->ninv_w_p = shoup(ninv_w, q, narrow);
     ld->narrow = narrow ? 1u : 0u;
-    ld->pad = 0;
+    int Q = 0;
+    while (Q < 64 && (q >> Q)) ++Q;   // bit length; q is an odd prime, so q > 2^(Q-1)
+    ld->barrett_qm1 = (uint32_t)(Q - 1);
+    ld->barrett_k = (uint64_t)(((u128)1 << (63 + Q)) / q);
 }
 
 // Untuned default schedules (the autotuner replaces them per workload).  For

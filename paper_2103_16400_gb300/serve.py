@@ -1,0 +1,292 @@
+"""Continuous-batching server for negacyclic polynomial products.
+
+A request is one product c = a * b in R_q = Z_q[X]/(X^N + 1) over an RNS
+basis (a, b: uint64 [limbs][N] residues), computed as in the paper's
+Listing 4: forward NTT of both operands with outputs left in [0, 4q),
+EltwiseMultMod with input_mod_factor 4, inverse NTT to [0, q).
+
+The paper's polynomial layer is single-threaded and per call (Section 3);
+its integration section notes that one call is too small to offload to an
+accelerator (Section 4).  The server answers that by batching: an engine
+thread repeatedly
+  1. moves newly submitted requests to a FIFO wait list,
+  2. admits waiting requests in order while their device memory (operands,
+     one result per request, in HBM) fits the HBM budget and a stream slot
+     is free -- requests that arrive while earlier batches are still on the
+     GPU join the next batch (continuous batching),
+  3. launches the admitted batch on its own CUDA stream as one ragged
+     product call (hx_polymul_ragged: five kernels for the whole batch,
+     whatever its mix of N and moduli) into a workspace taken from the
+     torch allocator, with one upload and one download for host operands,
+  4. completes the requests of every batch whose end event has fired,
+     stamping their latency, and releases their budget.
+Batches on different streams overlap on the GPU.  Plans (and so the twiddle
+tables) are created once per (N, moduli) and stay resident.
+
+All arithmetic runs in the CUDA library; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import queue
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import capi
+
+
+@dataclass
+class Request:
+    """a, b: uint64 [limbs][N] residues in [0, q) -- numpy arrays on the host
+    (the result comes back as a numpy array) or int64-typed CUDA tensors
+    resident in HBM (the result is a CUDA tensor view, nothing leaves the
+    device)."""
+    N: int
+    moduli: Tuple[int, ...]
+    a: object
+    b: object
+    arrival: float = 0.0             # perf_counter() at submission
+    done: float = 0.0
+    result: object = None
+    future: Future = field(default_factory=Future)
+
+    @property
+    def limbs(self) -> int:
+        return len(self.moduli)
+
+    @property
+    def resident(self) -> bool:
+        return not isinstance(self.a, np.ndarray)
+
+    @property
+    def device_bytes(self) -> int:
+        """HBM the request holds while in flight: two spectra in the batch
+        workspace and the result, plus the staged operands when they come
+        from the host (tile lists add 32 bytes per 2048 coefficients)."""
+        words = self.limbs * self.N
+        return (3 + (0 if self.resident else 2)) * words * 8 + (3 * words // 2048 + 4) * 64
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+class BudgetError(ValueError):
+    pass
+
+
+class Server:
+    """Engine thread + streams; `submit()` is thread-safe and returns a
+    Future that resolves to the product (uint64 [limbs][N])."""
+
+    def __init__(self, hbm_budget: int = 64 << 30, streams: int = 3,
+                 max_batch: int = 256, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.budget = int(hbm_budget)
+        self.max_batch = max_batch
+        torch.cuda.set_device(device)
+        capi.load()
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
+        self.free_streams = list(range(streams))
+        self.in_use = 0
+        self.plans: Dict[Tuple[int, Tuple[int, ...]], capi.Plan] = {}
+        self.inbox: "queue.Queue[Request]" = queue.Queue()
+        self.waiting: "collections.deque[Request]" = collections.deque()
+        self.inflight: List[dict] = []
+        self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "launches": 0}
+        self._stop = threading.Event()
+        self._thread: Optional[threading.Thread] = None
+        self._error: Optional[BaseException] = None
+
+    # ------------------------------------------------------------ client side
+    def plan(self, N: int, moduli: Sequence[int]) -> "capi.Plan":
+        key = (N, tuple(int(q) for q in moduli))
+        p = self.plans.get(key)
+        if p is None:
+            p = self.plans[key] = capi.Plan(N, key[1])
+        return p
+
+    def submit(self, req: Request) -> Future:
+        if req.device_bytes > self.budget:
+            raise BudgetError(f"request needs {req.device_bytes} bytes, budget {self.budget}")
+        req.arrival = time.perf_counter()
+        self.inbox.put(req)
+        return req.future
+
+    def start(self) -> "Server":
+        self._thread = threading.Thread(target=self._run, name="hexgpu-serve", daemon=True)
+        self._thread.start()
+        return self
+
+    def stop(self, drain: bool = True):
+        if drain:
+            while (not self.inbox.empty() or self.waiting or self.inflight) and self._error is None:
+                time.sleep(0.0005)
+        self._stop.set()
+        if self._thread:
+            self._thread.join()
+        if self._error is not None:
+            raise self._error
+
+    def __enter__(self):
+        return self.start()
+
+    def __exit__(self, *exc):
+        self.stop(drain=exc[0] is None)
+
+    # ------------------------------------------------------------ engine
+    def _run(self):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        try:
+            while not self._stop.is_set():
+                moved = self._drain_inbox()
+                self._complete_finished()
+                launched = self._admit_and_launch()
+                if not (moved or launched):
+                    time.sleep(0.0001)
+        except BaseException as e:              # surface engine errors to the client
+            self._error = e
+            for r in list(self.waiting):
+                r.future.set_exception(e)
+            for b in self.inflight:
+                for r in b["reqs"]:
+                    r.future.set_exception(e)
+
+    def _drain_inbox(self) -> bool:
+        moved = False
+        while True:
+            try:
+                self.waiting.append(self.inbox.get_nowait())
+                moved = True
+            except queue.Empty:
+                return moved
+
+    def _admit_and_launch(self) -> bool:
+        if not self.waiting or not self.free_streams:
+            return False
+        batch, need = [], 0
+        while self.waiting and len(batch) < self.max_batch:
+            r = self.waiting[0]
+            if self.in_use + need + r.device_bytes > self.budget:
+                break
+            batch.append(self.waiting.popleft())
+            need += r.device_bytes
+        if not batch:
+            return False
+        self.in_use += need
+        sid = self.free_streams.pop()
+        self.inflight.append(self._launch(batch, sid, need))
+        return True
+
+    def _launch(self, reqs: List[Request], sid: int, need: int) -> dict:
+        torch = self.torch
+        stream = self.streams[sid]
+        dev_name = f"cuda:{self.device}"
+        sizes = [r.limbs * r.N for r in reqs]
+        res_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        host_reqs = [k for k, r in enumerate(reqs) if not r.resident]
+        with torch.cuda.stream(stream):
+            res = torch.empty(int(res_off[-1]), dtype=torch.int64, device=dev_name)
+            staged = pinned = None
+            in_off = {}
+            if host_reqs:
+                # all host operands through one pinned buffer and one upload
+                total = 2 * sum(sizes[k] for k in host_reqs)
+                pinned = torch.empty(total, dtype=torch.int64, pin_memory=True)
+                pv = pinned.numpy().view(np.uint64)
+                o = 0
+                for k in host_reqs:
+                    r, s = reqs[k], sizes[k]
+                    pv[o:o + s] = r.a.reshape(-1)
+                    pv[o + s:o + 2 * s] = r.b.reshape(-1)
+                    in_off[k] = o
+                    o += 2 * s
+                staged = pinned.to(dev_name, non_blocking=True)
+            items = []
+            for k, r in enumerate(reqs):
+                out = res[int(res_off[k]):int(res_off[k + 1])]
+                if r.resident:
+                    a, b = r.a, r.b
+                else:
+                    o, s = in_off[k], sizes[k]
+                    a, b = staged[o:o + s], staged[o + s:o + 2 * s]
+                items.append((self.plan(r.N, r.moduli), a, b, out, 1))
+            arr = capi.polymul_items(items)
+            wsb = capi.hx_polymul_ragged_workspace(arr)
+            ws = torch.empty(wsb, dtype=torch.uint8, device=dev_name)
+            capi.hx_polymul_ragged(arr, ws, wsb, stream.cuda_stream)
+            out_host = None
+            if host_reqs:
+                out_host = torch.empty(int(res_off[-1]), dtype=torch.int64, pin_memory=True)
+                out_host.copy_(res, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.stats["batches"] += 1
+        self.stats["requests"] += len(reqs)
+        self.stats["launches"] += 5
+        self.stats["max_batch"] = max(self.stats["max_batch"], len(reqs))
+        work = (res, res_off, out_host, staged, pinned, ws)
+        return {"reqs": reqs, "work": work, "event": ev, "sid": sid, "bytes": need}
+
+    def _complete_finished(self):
+        still = []
+        for b in self.inflight:
+            if not b["event"].query():
+                still.append(b)
+                continue
+            now = time.perf_counter()
+            res, res_off, out_host, _, _, _ = b["work"]
+            hv = out_host.numpy().view(np.uint64) if out_host is not None else None
+            for k, r in enumerate(b["reqs"]):
+                lo, hi = int(res_off[k]), int(res_off[k + 1])
+                if r.resident:
+                    r.result = res[lo:hi].view(r.limbs, r.N)
+                else:
+                    r.result = hv[lo:hi].reshape(r.limbs, r.N).copy()
+                r.done = now
+                r.future.set_result(r.result)
+            self.in_use -= b["bytes"]
+            self.free_streams.append(b["sid"])
+        self.inflight = still
+
+
+def serve_one_by_one(reqs: Sequence[Request], arrivals: Optional[Sequence[float]] = None,
+                     plans: Optional[dict] = None, device: int = 0) -> None:
+    """The unbatched baseline: each request alone, in arrival order, with the
+    plain per-request calls (upload, hx_poly_mul, download, wait).  When
+    `arrivals` (offsets in seconds) are given, a request does not start
+    before its arrival time; latency counts from arrival."""
+    import torch
+    plans = {} if plans is None else plans
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        if arrivals is not None:
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            r.arrival = t0 + arrivals[i]
+        else:
+            r.arrival = time.perf_counter()
+        key = (r.N, tuple(r.moduli))
+        if key not in plans:
+            plans[key] = capi.Plan(r.N, key[1])
+        if r.resident:
+            a, b = r.a.clone(), r.b.clone()         # hx_poly_mul overwrites its operands
+        else:
+            a = torch.from_numpy(r.a.view(np.int64)).to(f"cuda:{device}", non_blocking=True)
+            b = torch.from_numpy(r.b.view(np.int64)).to(f"cuda:{device}", non_blocking=True)
+        capi.hx_poly_mul(plans[key], a, a, b, 1, stream.cuda_stream)
+        if r.resident:
+            stream.synchronize()
+            r.result = a
+        else:
+            r.result = a.cpu().numpy().view(np.uint64)
+        r.done = time.perf_counter()
