@@ -108,17 +108,19 @@ int hx_plan_info(hx_plan_t plan, uint64_t* N, uint32_t* n_limbs, uint64_t* devic
 /* Kernel schedule of the plan's transforms -- the knob the autotuner turns;
  * any valid schedule gives identical results, only speed differs (the paper
  * suggests choosing implementations by trials, Section 3.2).  npass is 1 or
- * 2; params holds six int32 per pass, in stage order:
- *   {s0, K, logGb, logGc, logR, pipe}
+ * 2; params holds seven int32 per pass, in stage order:
+ *   {s0, K, logGb, logGc, logR, pipe, np}
  * pass covers stages [s0, s0 + K) of the log2 N stages; a tile is
  * 2^logGb x 2^K x 2^logGc elements (top-index values x stage bits x
  * low-index values); 2^logR elements per thread; pipe = 1 selects the
- * persistent double-buffered kernel.  hx_plan_set_schedule returns
- * HX_ERR_ARG for a schedule the library cannot run (stages not covering
- * [0, log2 N), unsupported K or logR, tile too large).  `direction` selects
- * the forward (1) or inverse (2) transform's schedule, or both (3, set
- * only); the inverse runs the same passes in reverse order.
- * hx_plan_get_schedule writes 12 int32 (the unused second pass zeroed). */
+ * persistent double-buffered kernel; np (1 or 2) is the number of
+ * polynomials each thread transforms with one set of twiddle registers.
+ * hx_plan_set_schedule returns HX_ERR_ARG for a schedule the library cannot
+ * run (stages not covering [0, log2 N), a kernel not in the menu, tile too
+ * large).  `direction` selects the forward (1) or inverse (2) transform's
+ * schedule, or both (3, set only); the inverse runs the same passes in
+ * reverse order.  hx_plan_get_schedule writes 14 int32 (the unused second
+ * pass zeroed). */
 int hx_plan_set_schedule(hx_plan_t plan, uint32_t direction, uint32_t npass,
                          const int32_t* params);
 int hx_plan_get_schedule(hx_plan_t plan, uint32_t direction, uint32_t* npass, int32_t* params);

@@ -148,11 +148,11 @@ class Plan:
 
     def schedule(self, direction: int = 1):
         """Kernel schedule of the forward (1) or inverse (2) transform: a list
-        of (s0, K, logGb, logGc, logR, pipe) per pass."""
-        n, p = U32(), (ctypes.c_int32 * 12)()
+        of (s0, K, logGb, logGc, logR, pipe, np) per pass."""
+        n, p = U32(), (ctypes.c_int32 * 14)()
         _check("hx_plan_get_schedule",
                load().hx_plan_get_schedule(self.handle, direction, ctypes.byref(n), p))
-        return [tuple(p[6 * i:6 * i + 6]) for i in range(n.value)]
+        return [tuple(p[7 * i:7 * i + 7]) for i in range(n.value)]
 
     def set_schedule(self, passes, direction: int = 3):
         flat = [int(v) for ps in passes for v in ps]

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256, 2) ragged_pass_kernel(const RagTile* __re
     }
 }
 
-static const size_t kRagSmem = 2048 * sizeof(uint64_t);
+static const size_t kRagSmem = padded(2048) * sizeof(uint64_t);
 
 }  // namespace hx
 

@@ -7,7 +7,7 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/hexgpu.h"
+#include "hexgpu.h"   // include/ is on the include path
 
 namespace hx {
 
@@ -27,9 +27,10 @@ struct LimbDev {
 // One pass of a transform: CT stages [s0, s0 + K) on tiles of
 // 2^logGb (top-index values) x 2^K x 2^logGc (low-index values) elements,
 // 2^logR elements per thread; pipe selects the persistent double-buffered
-// kernel (1) or one block per tile (0).
+// kernel (1) or one block per tile (0); np = polynomials per thread sharing
+// one set of twiddle registers (1 or 2; 2 only with logR 3 and pipe 0).
 struct PassCfg {
-    int s0, K, logGb, logGc, logR, pipe;
+    int s0, K, logGb, logGc, logR, pipe, np;
 };
 
 struct NttCfg {

@@ -20,8 +20,13 @@ namespace hx {
 static PassKernel pick(bool fwd, const PassCfg& p) {
     const bool column = p.logGc > 0;
     if (p.pipe)
-        return fwd ? pick_fwd_pipe(column, p.logR, p.K) : pick_inv_pipe(column, p.logR, p.K);
-    return fwd ? pick_fwd(column, p.logR, p.K) : pick_inv(column, p.logR, p.K);
+        return p.np != 1 ? nullptr
+                         : fwd ? pick_pipe_f(column, p.logR, p.K) : pick_pipe_i(column, p.logR, p.K);
+    if (p.np == 2)
+        return fwd ? pick_plain_f2(column, p.logR, p.K) : pick_plain_i2(column, p.logR, p.K);
+    if (p.np == 1)
+        return fwd ? pick_plain_f1(column, p.logR, p.K) : pick_plain_i1(column, p.logR, p.K);
+    return nullptr;
 }
 
 static bool pass_ok(int L, const PassCfg& p) {
@@ -36,7 +41,8 @@ static bool pass_ok(int L, const PassCfg& p) {
     const int logTE = p.logGb + p.K + p.logGc;
     const int logT = logTE - p.logR;
     if (logT < 5 || logT > (p.pipe ? 8 : 9)) return false;      // 32 .. 256 / 512 threads
-    const size_t smem = (size_t)(p.pipe ? 16 : 8) << logTE;
+    const size_t smem = p.pipe ? (size_t)16 << logTE
+                                    : (size_t)8 * p.np * padded(1u << logTE);
     if (smem > 192 * 1024) return false;
     return true;
 }
@@ -94,7 +100,8 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
         const int logTE = p.logGb + p.K + p.logGc;
         const uint32_t tiles = 1u << (L - logTE);
         const uint32_t threads = 1u << (logTE - p.logR);
-        const size_t smem = (size_t)(p.pipe ? 16 : 8) << logTE;
+        const size_t smem = p.pipe ? (size_t)16 << logTE
+                                    : (size_t)8 * p.np * padded(1u << logTE);
         PassKernel k = pick(forward, p);
         if (!k) return cudaErrorInvalidConfiguration;
         if (smem > 48 * 1024) {
@@ -110,7 +117,7 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
             const uint64_t grid = std::min<uint64_t>(total, (uint64_t)per_sm * sms);
             k<<<(unsigned)grid, threads, smem, stream>>>(a);
         } else {
-            dim3 grid(tiles * n_polys, plan->n_limbs);
+            dim3 grid(tiles * ((n_polys + p.np - 1) / p.np), plan->n_limbs);
             k<<<grid, threads, smem, stream>>>(a);
         }
         count_launch();

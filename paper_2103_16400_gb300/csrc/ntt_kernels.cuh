@@ -59,10 +59,15 @@ struct Sched {
     }
 };
 
-// Shared-memory position of local element l: XOR bits 0..3 with bits 4..7 so
-// that column-wise and stride-2^r row-wise half-warp accesses hit distinct
-// 8-byte bank pairs.
-__device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 4) & 15u); }
+// Shared-memory position of local element l in the per-tile kernels: one pad
+// word after every 16, so column-wise and stride-2^r row-wise half-warp
+// accesses hit distinct 8-byte bank pairs.  For a register offset v << s
+// (disjoint from the group's base bits) the position is
+// pad(base) + (v << s) + ((v << s) >> 4): a compile-time constant whenever s
+// is, so those accesses need no address arithmetic.
+__device__ __forceinline__ uint32_t pad(uint32_t l) { return l + (l >> 4); }
+__host__ __device__ constexpr uint32_t padded(uint32_t te) { return te + (te >> 4); }
+__device__ __forceinline__ uint32_t pad_off(uint32_t v, int s) { return (v << s) + ((v << s) >> 4); }
 
 template <typename Wd>
 struct Word;
@@ -108,6 +113,8 @@ struct TileCtx {
     uint32_t nthreads;
     uint32_t out_mf;
     bool last;
+    uint64_t poly_stride = 0;   // elements between the same limb of consecutive polynomials
+    uint32_t np_valid = 1;      // polynomials of this block's group that exist
 };
 
 // Global index of local tile element l = (bl, e, cl).
@@ -128,13 +135,18 @@ enum { IO_SMEM = 0, IO_GLOBAL = 1 };
 // reg = (v << (LOG_R - R)) | u, so the butterfly pair of sub-stage k differs
 // in register bit LOG_R-1-k (a compile-time position).  Group g = u * T + tid
 // (T threads) has bits [bl | e_hi (P) | e_lo (K-P-R) | cl (logGc)].
-template <bool FWD, typename Wd, int LOG_R, int K, int P, int R, int SRC, int DST>
+// With NP > 1 the thread holds the same positions of NP polynomials (same
+// limb, same twiddles): every twiddle pair it loads serves NP butterflies.
+// Polynomial p's tile lives at sm + p * TE in shared memory.
+template <bool FWD, typename Wd, int LOG_R, int K, int P, int R, int SRC, int DST, int NP = 1,
+          bool ROW = false>
 __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                           const LimbDev& lc, const TileCtx& c) {
     constexpr int RN = 1 << LOG_R;
     constexpr int U = 1 << (LOG_R - R);
     constexpr int ELO = K - P - R;
-    Wd x[RN];
+    const uint32_t TEP = padded(c.nthreads << LOG_R);
+    Wd xs[NP][RN];
     uint64_t pfx[U];
     uint32_t lbase[U];
     const uint32_t cmask = (1u << c.logGc) - 1;
@@ -150,22 +162,35 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         lbase[u] = (bl << (K + c.logGc)) | (ehi << (K - P + c.logGc)) | (elo << c.logGc) | cl;
         pfx[u] = ((c.b_base + bl) << P) | ehi;
     }
-    const int sshift = ELO + c.logGc;   // v stride in the tile
-    const int gshift = ELO + c.w;       // v stride in global memory
+    const int sshift = ROW ? ELO : ELO + c.logGc;   // v stride in the tile
+    const int gshift = ELO + c.w;                   // v stride in global memory
+    uint32_t pl[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) pl[u] = pad(lbase[u]);
 
-    if (SRC == IO_GLOBAL) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint64_t* p = c.gin + tile_gidx<K>(lbase[u], c);
+    for (int pp = 0; pp < NP; ++pp) {
+        Wd* x = xs[pp];
+        if (NP > 1 && pp >= (int)c.np_valid) {   // no such polynomial: idle registers
 #pragma unroll
-            for (int v = 0; v < (1 << R); ++v)
-                x[(v << (LOG_R - R)) | u] = (Wd)__ldg(p + ((uint64_t)v << gshift));
+            for (int reg = 0; reg < RN; ++reg) x[reg] = 0;
+            continue;
         }
-    } else {
+        if (SRC == IO_GLOBAL) {
 #pragma unroll
-        for (int reg = 0; reg < RN; ++reg) {
-            const int u = reg & (U - 1), v = reg >> (LOG_R - R);
-            x[reg] = (Wd)sm[swz(lbase[u] + ((uint32_t)v << sshift))];
+            for (int u = 0; u < U; ++u) {
+                const uint64_t* p = c.gin + pp * c.poly_stride + tile_gidx<K>(lbase[u], c);
+#pragma unroll
+                for (int v = 0; v < (1 << R); ++v)
+                    x[(v << (LOG_R - R)) | u] = (Wd)__ldg(p + ((uint64_t)v << gshift));
+            }
+        } else {
+            const uint64_t* smp = sm + pp * TEP;
+#pragma unroll
+            for (int reg = 0; reg < RN; ++reg) {
+                const int u = reg & (U - 1), v = reg >> (LOG_R - R);
+                x[reg] = (Wd)smp[pl[u] + pad_off(v, sshift)];
+            }
         }
     }
 
@@ -178,14 +203,17 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         if (!FWD && P == 0 && k == 0 && c.s0 == 0) {
             // stage 0 of the inverse: N^-1 folded into the last butterfly
 #pragma unroll
-            for (int reg0 = 0; reg0 < RN; ++reg0) {
-                if (reg0 & (1 << hb)) continue;
-                const int reg1 = reg0 | (1 << hb);
-                const Wd a = x[reg0], b = x[reg1];
-                const Wd sum = a + b;              // [0, 4q)
-                const Wd dif = a - b + (Wd)q2;     // (0, 4q)
-                x[reg0] = Word<Wd>::mul(sum, lc.ninv, lc.ninv_p, q);
-                x[reg1] = Word<Wd>::mul(dif, lc.ninv_w, lc.ninv_w_p, q);
+            for (int pp = 0; pp < NP; ++pp) {
+#pragma unroll
+                for (int reg0 = 0; reg0 < RN; ++reg0) {
+                    if (reg0 & (1 << hb)) continue;
+                    const int reg1 = reg0 | (1 << hb);
+                    const Wd a = xs[pp][reg0], b = xs[pp][reg1];
+                    const Wd sum = a + b;              // [0, 4q)
+                    const Wd dif = a - b + (Wd)q2;     // (0, 4q)
+                    xs[pp][reg0] = Word<Wd>::mul(sum, lc.ninv, lc.ninv_p, q);
+                    xs[pp][reg1] = Word<Wd>::mul(dif, lc.ninv_w, lc.ninv_w_p, q);
+                }
             }
             continue;
         }
@@ -198,56 +226,75 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
             const int reg1 = reg0 | (1 << hb);
             const int u = reg0 & (U - 1), v0 = reg0 >> (LOG_R - R);
             const ulonglong2 w = __ldg(tb[u] + (v0 >> (R - k)));
-            if (FWD)
-                Word<Wd>::fwd(x[reg0], x[reg1], w, q, q2);
-            else
-                Word<Wd>::inv(x[reg0], x[reg1], w, q, q2);
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+                if (FWD)
+                    Word<Wd>::fwd(xs[pp][reg0], xs[pp][reg1], w, q, q2);
+                else
+                    Word<Wd>::inv(xs[pp][reg0], xs[pp][reg1], w, q, q2);
+            }
         }
     }
     if (c.last && c.out_mf == 1) {
 #pragma unroll
-        for (int reg = 0; reg < RN; ++reg) {
-            Wd y = x[reg];
-            if (FWD) y = y >= (Wd)q2 ? y - (Wd)q2 : y;
-            x[reg] = y >= (Wd)q ? y - (Wd)q : y;
+        for (int pp = 0; pp < NP; ++pp) {
+#pragma unroll
+            for (int reg = 0; reg < RN; ++reg) {
+                Wd y = xs[pp][reg];
+                if (FWD) y = y >= (Wd)q2 ? y - (Wd)q2 : y;
+                xs[pp][reg] = y >= (Wd)q ? y - (Wd)q : y;
+            }
         }
     }
 
-    if (DST == IO_GLOBAL) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            uint64_t* p = c.gout + tile_gidx<K>(lbase[u], c);
+    for (int pp = 0; pp < NP; ++pp) {
+        if (NP > 1 && pp >= (int)c.np_valid) continue;
+        const Wd* x = xs[pp];
+        if (DST == IO_GLOBAL) {
 #pragma unroll
-            for (int v = 0; v < (1 << R); ++v)
-                p[(uint64_t)v << gshift] = (uint64_t)x[(v << (LOG_R - R)) | u];
-        }
-    } else {
+            for (int u = 0; u < U; ++u) {
+                uint64_t* p = c.gout + pp * c.poly_stride + tile_gidx<K>(lbase[u], c);
 #pragma unroll
-        for (int reg = 0; reg < RN; ++reg) {
-            const int u = reg & (U - 1), v = reg >> (LOG_R - R);
-            sm[swz(lbase[u] + ((uint32_t)v << sshift))] = (uint64_t)x[reg];
+                for (int v = 0; v < (1 << R); ++v)
+                    p[(uint64_t)v << gshift] = (uint64_t)x[(v << (LOG_R - R)) | u];
+            }
+        } else {
+            uint64_t* smp = sm + pp * TEP;
+#pragma unroll
+            for (int reg = 0; reg < RN; ++reg) {
+                const int u = reg & (U - 1), v = reg >> (LOG_R - R);
+                smp[pl[u] + pad_off(v, sshift)] = (uint64_t)x[reg];
+            }
         }
     }
 }
 
-// Cooperative coalesced copies of the whole tile between HBM and shared memory.
-template <int K>
+// Cooperative coalesced copies of the whole tile (of each of the block's NP
+// polynomials) between HBM and shared memory.
+template <int K, int NP = 1>
 __device__ __forceinline__ void tile_to_smem(uint64_t* sm, const TileCtx& c, uint32_t TE) {
-    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(c.gin);
-    for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
-        const uint32_t l = 2 * i;
-        const ulonglong2 v = __ldg(src + (tile_gidx<K>(l, c) >> 1));
-        sm[swz(l)] = v.x;
-        sm[swz(l + 1)] = v.y;
+    for (uint32_t pp = 0; pp < (NP > 1 ? c.np_valid : 1u); ++pp) {
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(c.gin + pp * c.poly_stride);
+        uint64_t* smp = sm + pp * padded(TE);
+        for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
+            const uint32_t l = 2 * i;
+            const ulonglong2 v = __ldg(src + (tile_gidx<K>(l, c) >> 1));
+            smp[pad(l)] = v.x;        // l even: l and l + 1 share one 16-word row
+            smp[pad(l) + 1] = v.y;
+        }
     }
 }
 
-template <int K>
+template <int K, int NP = 1>
 __device__ __forceinline__ void smem_to_tile(const uint64_t* sm, const TileCtx& c, uint32_t TE) {
-    ulonglong2* dst = reinterpret_cast<ulonglong2*>(c.gout);
-    for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
-        const uint32_t l = 2 * i;
-        dst[tile_gidx<K>(l, c) >> 1] = make_ulonglong2(sm[swz(l)], sm[swz(l + 1)]);
+    for (uint32_t pp = 0; pp < (NP > 1 ? c.np_valid : 1u); ++pp) {
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(c.gout + pp * c.poly_stride);
+        const uint64_t* smp = sm + pp * padded(TE);
+        for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
+            const uint32_t l = 2 * i;
+            dst[tile_gidx<K>(l, c) >> 1] = make_ulonglong2(smp[pad(l)], smp[pad(l) + 1]);
+        }
     }
 }
 
@@ -256,7 +303,7 @@ __device__ __forceinline__ void smem_to_tile(const uint64_t* sm, const TileCtx& 
 // rounds; row passes do so at their low-stage end only (the forward's first
 // round, the inverse's last) and stage the high-stage end through shared
 // memory, where the round's thread map is strided.
-template <bool FWD, bool COLUMN, typename Wd, int LOG_R, int K, int I>
+template <bool FWD, bool COLUMN, typename Wd, int LOG_R, int K, int I, int NP = 1>
 __device__ __forceinline__ void ntt_rounds(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                            const LimbDev& lc, const TileCtx& c) {
     using S = Sched<K, LOG_R>;
@@ -268,42 +315,45 @@ __device__ __forceinline__ void ntt_rounds(uint64_t* sm, const ulonglong2* __res
     TileCtx cr = c;
     cr.last = c.last && lastr;
     ntt_round<FWD, Wd, LOG_R, K, S::off(idx), S::size(idx), direct_in ? IO_GLOBAL : IO_SMEM,
-              direct_out ? IO_GLOBAL : IO_SMEM>(sm, tw, lc, cr);
+              direct_out ? IO_GLOBAL : IO_SMEM, NP, !COLUMN>(sm, tw, lc, cr);
     if constexpr (!lastr) {
         __syncthreads();
-        ntt_rounds<FWD, COLUMN, Wd, LOG_R, K, I + 1>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, Wd, LOG_R, K, I + 1, NP>(sm, tw, lc, c);
     }
 }
 
-// One tile of one pass, by the whole block (TE >> LOG_R threads): stage in
-// through shared memory where the first round's map is strided, run the
-// rounds, stage out where the last round's map is strided.
-template <bool FWD, bool COLUMN, int LOG_R, int K>
+// One tile of one pass (for each of NP polynomials), by the whole block
+// (TE >> LOG_R threads): stage in through shared memory where the first
+// round's map is strided, run the rounds, stage out where the last round's
+// map is strided.
+template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1>
 __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, const LimbDev& lc,
                                              uint32_t TE) {
     constexpr bool staged_in = !COLUMN && !FWD;
     constexpr bool staged_out = !COLUMN && FWD;
     if (staged_in) {
-        tile_to_smem<K>(sm, c, TE);
+        tile_to_smem<K, NP>(sm, c, TE);
         __syncthreads();
     }
     const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
     if (lc.narrow)
-        ntt_rounds<FWD, COLUMN, uint32_t, LOG_R, K, 0>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, uint32_t, LOG_R, K, 0, NP>(sm, tw, lc, c);
     else
-        ntt_rounds<FWD, COLUMN, uint64_t, LOG_R, K, 0>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, uint64_t, LOG_R, K, 0, NP>(sm, tw, lc, c);
     if (staged_out) {
         __syncthreads();
-        smem_to_tile<K>(sm, c, TE);
+        smem_to_tile<K, NP>(sm, c, TE);
     }
 }
 
-template <bool FWD, bool COLUMN, int LOG_R, int K>
+// One block per (tile, group of NP polynomials, limb).
+template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1>
 __global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
     extern __shared__ uint64_t sm[];
     const uint32_t limb = blockIdx.y;
-    const uint32_t poly = blockIdx.x % a.n_polys;
-    const uint32_t tile = blockIdx.x / a.n_polys;
+    const uint32_t n_groups = (a.n_polys + NP - 1) / NP;
+    const uint32_t poly = (blockIdx.x % n_groups) * NP;
+    const uint32_t tile = blockIdx.x / n_groups;
     const LimbDev lc = a.limbs[limb];
     const uint64_t base = ((uint64_t)poly * a.n_limbs + limb) << a.L;
     const uint32_t tile_c = tile & ((1u << a.log_tiles_c) - 1);
@@ -321,7 +371,9 @@ __global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
     c.nthreads = TE >> LOG_R;
     c.out_mf = a.out_mf;
     c.last = a.last != 0;
-    process_tile<FWD, COLUMN, LOG_R, K>(sm, c, lc, TE);
+    c.poly_stride = (uint64_t)a.n_limbs << a.L;
+    c.np_valid = min((uint32_t)NP, a.n_polys - poly);
+    process_tile<FWD, COLUMN, LOG_R, K, NP>(sm, c, lc, TE);
 }
 
 // ---------------------------------------------------------------------------
@@ -563,9 +615,13 @@ __global__ void __launch_bounds__(256, 2) ntt_pipe_kernel(PassArgs a) {
 typedef void (*PassKernel)(PassArgs);
 
 // ntt_fwd.cu / ntt_inv.cu
-PassKernel pick_fwd(bool column, int logR, int K);
-PassKernel pick_inv(bool column, int logR, int K);
-PassKernel pick_fwd_pipe(bool column, int logR, int K);
-PassKernel pick_inv_pipe(bool column, int logR, int K);
+// ntt_f1.cu, ntt_f2.cu, ntt_i1.cu, ntt_i2.cu: plain kernels with 1 or 2
+// polynomials per thread, and the persistent kernels (nullptr: not in the menu)
+PassKernel pick_plain_f1(bool column, int logR, int K);
+PassKernel pick_plain_f2(bool column, int logR, int K);
+PassKernel pick_plain_i1(bool column, int logR, int K);
+PassKernel pick_plain_i2(bool column, int logR, int K);
+PassKernel pick_pipe_f(bool column, int logR, int K);
+PassKernel pick_pipe_i(bool column, int logR, int K);
 
 }  // namespace hx

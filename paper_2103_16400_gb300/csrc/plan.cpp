@@ -126,13 +126,13 @@ NttCfg default_cfg(int logN, bool forward) {
     NttCfg c{};
     if (logN <= 13) {
         c.npass = 1;
-        c.pass[0] = PassCfg{0, logN, 0, 0, logN <= 12 ? 3 : 4, 0};
+        c.pass[0] = PassCfg{0, logN, 0, 0, logN <= 12 ? 3 : 4, 0, 1};
     } else {
         const int K1 = logN / 2, K2 = logN - K1;
         c.npass = 2;
-        c.pass[0] = forward ? PassCfg{0, K1, 0, 3, 4, 0} : PassCfg{0, K1, 0, 2, 3, 0};
+        c.pass[0] = forward ? PassCfg{0, K1, 0, 3, 4, 0, 1} : PassCfg{0, K1, 0, 2, 3, 0, 1};
         const int logGb = std::max(forward ? 0 : 1, 8 - K2);
-        c.pass[1] = PassCfg{K1, K2, std::min(logGb, K1), 0, 3, 0};
+        c.pass[1] = PassCfg{K1, K2, std::min(logGb, K1), 0, 3, 0, 1};
     }
     return c;
 }
@@ -323,8 +323,8 @@ extern "C" int hx_plan_set_schedule(hx_plan_t p, uint32_t direction, uint32_t np
     NttCfg c{};
     c.npass = (int)npass;
     for (uint32_t i = 0; i < npass; ++i) {
-        const int32_t* q = params + 6 * i;
-        c.pass[i] = PassCfg{q[0], q[1], q[2], q[3], q[4], q[5]};
+        const int32_t* q = params + 7 * i;
+        c.pass[i] = PassCfg{q[0], q[1], q[2], q[3], q[4], q[5], q[6]};
     }
     if (!cfg_supported(p->logN, c)) return HX_ERR_ARG;
     if (direction & 1) p->cfg_fwd = c;
@@ -340,8 +340,8 @@ extern "C" int hx_plan_get_schedule(hx_plan_t p, uint32_t direction, uint32_t* n
     *npass = (uint32_t)cfg.npass;
     for (int i = 0; i < 2; ++i) {
         const PassCfg& c = cfg.pass[i];
-        const int32_t v[6] = {c.s0, c.K, c.logGb, c.logGc, c.logR, c.pipe};
-        memcpy(params + 6 * i, v, sizeof(v));
+        const int32_t v[7] = {c.s0, c.K, c.logGb, c.logGc, c.logR, c.pipe, c.np};
+        memcpy(params + 7 * i, v, sizeof(v));
     }
     return HX_OK;
 }

@@ -19,32 +19,33 @@ from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 
 from . import capi
 
-Pass = Tuple[int, int, int, int, int, int]     # s0, K, logGb, logGc, logR, pipe
+Pass = Tuple[int, int, int, int, int, int, int]   # s0, K, logGb, logGc, logR, pipe, np
 CACHE_PATH = os.environ.get("HX_TUNE_CACHE",
                             os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                          "_build", "tune_cache.json"))
 _lock = threading.Lock()
 
 
-def candidates(logN: int) -> List[List[Pass]]:
+#: per-pass kernel variants: (logR, pipe, np) -- 16 or 8 elements per thread,
+#: plain or persistent, one or two polynomials per thread
+VARIANTS = ((3, 0, 1), (4, 0, 1), (3, 1, 1), (4, 1, 1), (3, 0, 2))
+
+
+def candidates(logN: int, variants=VARIANTS) -> List[List[Pass]]:
     """Schedules worth trying for log2 N (validity is checked by the library)."""
     out: List[List[Pass]] = []
     if logN <= 13:
-        for logR in (3, 4):
-            for pipe in (0, 1):
-                out.append([(0, logN, 0, 0, logR, pipe)])
+        for logR, pipe, np_ in variants:
+            out.append([(0, logN, 0, 0, logR, pipe, np_)])
     for K1 in range(6, 10):
         K2 = logN - K1
         if not 6 <= K2 <= 13:
             continue
         for logGc in (2, 3, 4, 5):
-            for logR1 in (3, 4):
-                for pipe1 in (0, 1):
-                    for logGb in range(0, 6):
-                        for logR2 in (3, 4):
-                            for pipe2 in (0, 1):
-                                out.append([(0, K1, 0, logGc, logR1, pipe1),
-                                            (K1, K2, logGb, 0, logR2, pipe2)])
+            for v1 in variants:
+                for logGb in range(0, 6):
+                    for v2 in variants:
+                        out.append([(0, K1, 0, logGc) + v1, (K1, K2, logGb, 0) + v2])
     return out
 
 
