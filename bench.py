@@ -36,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
+from paper_2103_16400_gb300 import shard  # noqa: E402
 
 METRIC = "NTT limb-transforms/s at N=2^16 (% of int-mul/HBM roofline); served p99 latency"
 UNIT = "limb-transforms/s"
@@ -44,14 +45,16 @@ LIMBS_DEFAULT = 32
 
 
 # ------------------------------------------------------------------ workload
-def workload_arrays(N, n_limbs, n_sets):
+def workload_arrays(N, n_limbs, n_sets, rank=0):
     """n_sets input sets, each (ins, es): ins = [a0, a1, b0, b1], es = [e0, e1,
-    e2], every one a [1][n_limbs][N] uint64 array of uniform residues."""
+    e2], every one a [1][n_limbs][N] uint64 array of uniform residues.  Under
+    weak scaling each rank draws its own independent sets (same shapes)."""
     wl = W.ciphertext_tensor(N=N, n_limbs=n_limbs)
+    seed = shard.rank_seed(wl.seed, rank)
     sets = []
     for k in range(n_sets):
-        ins = [W.poly_batch(wl.seed + 1000 * k, t, 1, wl.moduli, N) for t in range(4)]
-        es = [W.poly_batch(wl.seed + 1000 * k, 10 + t, 1, wl.moduli, N) for t in range(3)]
+        ins = [W.poly_batch(seed + 1000 * k, t, 1, wl.moduli, N) for t in range(4)]
+        es = [W.poly_batch(seed + 1000 * k, 10 + t, 1, wl.moduli, N) for t in range(3)]
         sets.append((ins, es))
     s = W.scalars(wl.seed, 20, wl.moduli)
     return wl, sets, s
@@ -480,7 +483,7 @@ def main():
     ap.add_argument("--impl", default="hexgpu", choices=["hexgpu", "reference"])
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--limbs", type=int, default=LIMBS_DEFAULT)
-    ap.add_argument("--sets", type=int, default=3)
+    ap.add_argument("--sets", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ragged", action="store_true",
                     help="skip the ragged-batch report (512 polynomials, mixed N)")
@@ -510,7 +513,7 @@ def main():
     hbuild.build()
 
     N, nl = args.N, args.limbs
-    wl, sets, s = workload_arrays(N, nl, args.sets)
+    wl, sets, s = workload_arrays(N, nl, args.sets, rank)
     dev_sets = device_sets(sets)
     step = HexStep(N, wl.moduli, s, dev_sets, torch)
 
@@ -536,10 +539,7 @@ def main():
     launches = capi.hx_launch_count() - launches0
     total_ms = t0.elapsed_time(t1)
     fwd_ms = [a.elapsed_time(b) for a, b in step.fwd_events]
-    if ws > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = shard.max_over_ranks(total_ms, device="cuda")
     barrier()
 
     per_step_units = 7 * nl
@@ -589,10 +589,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = shard.max_over_ranks(e2e_ms, device="cuda")
     e2e_value = per_step_units * e2e_steps * ws / (e2e_ms / 1e3)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -611,15 +608,17 @@ def main():
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks.summary()}
-    if not args.no_ragged:
+    # the batched and serving reports run on rank 0 only; the other ranks wait
+    if rank == 0 and not args.no_ragged:
         line["batched"] = ragged_report(torch)
-    if not args.no_serving:
+    if rank == 0 and not args.no_serving:
         line["serving"] = serving_report(torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(N, wl.moduli, s, sets)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
+        torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
 
