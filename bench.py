@@ -424,7 +424,7 @@ def run_case(args):
             out[f"int_mul_{kind}_Tops"] = r / 1e12
         for w in W.WIDTHS:
             q = W.ntt_primes(w, W.MIXED_TWO_N, 1)[0]
-            for v in (0, 1, 2):
+            for v in (0, 1, 2, 3):
                 for inv in (False, True):
                     if w == 30 and v > 0:
                         continue
@@ -438,6 +438,10 @@ def run_case(args):
     xs = [to_device(W.poly_batch(wl.seed + k, 0, P, wl.moduli, N)) for k in range(n_sets)]
     ys = [empty(x.shape) for x in xs]
     plan = capi.Plan(N, wl.moduli)
+    if args.tuned and args.case in ("fwd", "inv"):
+        from paper_2103_16400_gb300 import tune as hx_tune
+        t = hx_tune.tune(plan, P, direction=plan.FORWARD if args.case == "fwd" else plan.INVERSE)
+        out["schedule"] = t["forward" if args.case == "fwd" else "inverse"]
     s = W.scalars(wl.seed, 20, wl.moduli)
     st = torch.cuda.current_stream()
 
@@ -495,6 +499,8 @@ def main():
                     help="pipeline: the contract line; others: one kernel family alone "
                          "(diagnostic line, used for profiling)")
     ap.add_argument("--polys", type=int, default=8, help="polynomials per call for --case fwd/inv")
+    ap.add_argument("--tuned", action="store_true",
+                    help="--case fwd/inv: apply the autotuned schedule (cached) instead of the default")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

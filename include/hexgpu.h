@@ -348,9 +348,10 @@ int hx_polymul_ragged(const hx_polymul_item* h_items, uint32_t n_items, void* d_
  * hx_probe_butterfly_rate: the same grid running Harvey butterflies for
  *   modulus q on register-resident data (4 per thread per iteration);
  *   `variant` bits 0-3 pick the 64-bit Shoup-product code (0: compiler's
- *   64-bit products, 1: mad.wide high word, 2: carry-chain high word), bit 4
- *   the inverse butterfly.  Returns butterflies per second.  Synchronises
- *   `stream`.
+ *   64-bit products, 1: mad.wide high word, 2: carry-chain high word, 3:
+ *   truncated high word from three partial products, lazy bound 4q, needs
+ *   q < 2^61), bit 4 the inverse butterfly.  Returns butterflies per second.
+ *   Synchronises `stream`.
  * Errors: HX_ERR_NULL, HX_ERR_ARG, HX_ERR_NOMEM, HX_ERR_CUDA.
  */
 uint64_t hx_launch_count(void);

@@ -22,6 +22,9 @@ struct LimbDev {
     uint32_t narrow;            // 1: q < 2^30, 32-bit words, beta = 2^32
     uint32_t barrett_qm1;       // bitlen(q) - 1 (Barrett shift)
     uint64_t barrett_k;         // floor(2^(63 + bitlen(q)) / q)
+    uint32_t trunc;             // 1: 64-bit words with q < 2^61 -- the NTT uses the
+                                // truncated-quotient Shoup product (values < 8q)
+    uint32_t pad_;
 };
 
 // One pass of a transform: CT stages [s0, s0 + K) on tiles of

@@ -88,16 +88,34 @@ __device__ __forceinline__ uint64_t shoup_rem64(uint64_t w, uint64_t x, uint64_t
     return ((uint64_t)th << 32) | (uint32_t)t;
 }
 
+// Truncated high word of a*b: a1 b1 + hi32(a1 b0) + hi32(a0 b1), from three of
+// the four partial products and no carry propagation out of the low word.
+// The dropped part, (lo32(a1 b0) + lo32(a0 b1)) 2^32 + a0 b0, is below
+// 3 * 2^64, so the result is floor(a b / 2^64) minus 0, 1 or 2.
+__device__ __forceinline__ uint64_t mulhi64_trunc(uint64_t a, uint64_t b) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint32_t h0, h1;
+    uint64_t r;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(h0) : "r"(a1), "r"(b0));
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(h1) : "r"(a0), "r"(b1));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a1), "r"(b1), "l"((uint64_t)h0));
+    return r + h1;
+}
+
 // Shoup product variants (V): 0 plain C++; 1 mad.wide high word + explicit
-// remainder; 2 carry-chain high word + explicit remainder.  All return the
-// same value, w x mod q in [0, 2q).
+// remainder; 2 carry-chain high word + explicit remainder -- all three return
+// the same value, w x mod q in [0, 2q); 3 truncated high word + explicit
+// remainder.  With Q' = Q - e (e <= 2) the remainder W X - Q' q is the exact
+// one plus e q, so variant 3 returns w x mod q in [0, 4q) (needs 4q < 2^64).
 template <int V>
 __device__ __forceinline__ uint64_t shoup_lazy64v(uint64_t x, uint64_t w, uint64_t wp, uint64_t q,
                                                   uint64_t nq) {
     if constexpr (V == 0) {
         return shoup_mul_lazy64(x, w, wp, q);
     } else {
-        const uint64_t Q = V == 1 ? mulhi64_wide(wp, x) : mulhi64_cc(wp, x);
+        const uint64_t Q = V == 1 ? mulhi64_wide(wp, x)
+                                  : V == 2 ? mulhi64_cc(wp, x) : mulhi64_trunc(wp, x);
         return shoup_rem64(w, x, Q, nq);
     }
 }
@@ -106,31 +124,34 @@ __device__ __forceinline__ uint64_t shoup_lazy64v(uint64_t x, uint64_t w, uint64
 #define HX_SHOUP_VARIANT 2
 #endif
 
-// x in [0, 4q) -> [0, 2q): subtract 2q unless that borrows.  Since 2q < 2^63
-// and x < 2^64, x - 2q wraps past 2^63 exactly when x < 2q, so the sign bit
-// of the difference decides.
+// x in [0, 2m) -> [0, m) (m = 2q or 4q): subtract m unless that borrows.
+// Since m <= 2^63 and x < 2m, x - m wraps past 2^63 exactly when x < m, so
+// the sign bit of the difference decides.
 __device__ __forceinline__ uint64_t reduce_2q(uint64_t x, uint64_t two_q) {
     const uint64_t d = x - two_q;
     return (int64_t)d < 0 ? x : d;
 }
 
-// Harvey forward butterfly: X0, X1 in [0, 4q) -> X0 + W X1, X0 - W X1 in [0, 4q).
+// Harvey forward butterfly with lazy bound m, the range of the Shoup product
+// (m = 2q for variants 0-2, m = 4q for variant 3):
+// X0, X1 in [0, 2m) -> X0 + W X1, X0 - W X1 in [0, 2m).  Needs 2m < 2^64.
 template <int V = HX_SHOUP_VARIANT>
 __device__ __forceinline__ void harvey_fwd64(uint64_t& X0, uint64_t& X1, uint64_t W,
-                                             uint64_t Wp, uint64_t q, uint64_t two_q) {
-    const uint64_t x0 = V == 0 ? (X0 >= two_q ? X0 - two_q : X0) : reduce_2q(X0, two_q);
+                                             uint64_t Wp, uint64_t q, uint64_t m) {
+    const uint64_t x0 = V == 0 ? (X0 >= m ? X0 - m : X0) : reduce_2q(X0, m);
     const uint64_t T = shoup_lazy64v<V>(X1, W, Wp, q, 0 - q);
     X0 = x0 + T;
-    X1 = x0 - T + two_q;
+    X1 = x0 - T + m;
 }
 
-// Harvey inverse butterfly: X0, X1 in [0, 2q) -> X0 + X1, W (X0 - X1) in [0, 2q).
+// Harvey inverse butterfly with lazy bound m (as above):
+// X0, X1 in [0, m) -> X0 + X1, W (X0 - X1) in [0, m).
 template <int V = HX_SHOUP_VARIANT>
 __device__ __forceinline__ void harvey_inv64(uint64_t& X0, uint64_t& X1, uint64_t W,
-                                             uint64_t Wp, uint64_t q, uint64_t two_q) {
+                                             uint64_t Wp, uint64_t q, uint64_t m) {
     uint64_t y0 = X0 + X1;
-    y0 = V == 0 ? (y0 >= two_q ? y0 - two_q : y0) : reduce_2q(y0, two_q);
-    const uint64_t T = X0 - X1 + two_q;
+    y0 = V == 0 ? (y0 >= m ? y0 - m : y0) : reduce_2q(y0, m);
+    const uint64_t T = X0 - X1 + m;
     X1 = shoup_lazy64v<V>(T, W, Wp, q, 0 - q);
     X0 = y0;
 }

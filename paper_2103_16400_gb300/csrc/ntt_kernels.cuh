@@ -69,40 +69,64 @@ __device__ __forceinline__ uint32_t pad(uint32_t l) { return l + (l >> 4); }
 __host__ __device__ constexpr uint32_t padded(uint32_t te) { return te + (te >> 4); }
 __device__ __forceinline__ uint32_t pad_off(uint32_t v, int s) { return (v << s) + ((v << s) >> 4); }
 
-template <typename Wd>
+// Word<Wd, AR>: butterflies on Wd-sized words.  AR = 0 uses the exact Shoup
+// product (lazy bound m = 2q: forward values in [0, 4q), inverse in [0, 2q),
+// the paper's ranges); AR = 1 (64-bit words, q < 2^61) uses the truncated
+// quotient, whose product lies in [0, 4q), so m = 4q: forward values in
+// [0, 8q), inverse in [0, 4q).  Either way every output is w x mod q
+// exactly; only the lazy representative differs.
+template <typename Wd, int AR = 0>
 struct Word;
 
-template <>
-struct Word<uint64_t> {
+template <int AR>
+struct Word<uint64_t, AR> {
+    static constexpr int V = AR ? 3 : HX_SHOUP_VARIANT;
+    static constexpr uint32_t M = AR ? 4 : 2;
     static __device__ __forceinline__ void fwd(uint64_t& a, uint64_t& b, ulonglong2 w, uint64_t q,
-                                               uint64_t q2) {
-        harvey_fwd64(a, b, w.x, w.y, q, q2);
+                                               uint64_t m) {
+        harvey_fwd64<V>(a, b, w.x, w.y, q, m);
     }
     static __device__ __forceinline__ void inv(uint64_t& a, uint64_t& b, ulonglong2 w, uint64_t q,
-                                               uint64_t q2) {
-        harvey_inv64(a, b, w.x, w.y, q, q2);
+                                               uint64_t m) {
+        harvey_inv64<V>(a, b, w.x, w.y, q, m);
     }
     static __device__ __forceinline__ uint64_t mul(uint64_t x, uint64_t w, uint64_t wp,
                                                    uint64_t q) {
-        return shoup_lazy64v<HX_SHOUP_VARIANT>(x, w, wp, q, 0 - q);
+        return shoup_lazy64v<V>(x, w, wp, q, 0 - q);
     }
 };
 
 template <>
-struct Word<uint32_t> {
+struct Word<uint32_t, 0> {
+    static constexpr uint32_t M = 2;
     static __device__ __forceinline__ void fwd(uint32_t& a, uint32_t& b, ulonglong2 w, uint64_t q,
-                                               uint64_t q2) {
-        harvey_fwd32(a, b, (uint32_t)w.x, (uint32_t)w.y, (uint32_t)q, (uint32_t)q2);
+                                               uint64_t m) {
+        harvey_fwd32(a, b, (uint32_t)w.x, (uint32_t)w.y, (uint32_t)q, (uint32_t)m);
     }
     static __device__ __forceinline__ void inv(uint32_t& a, uint32_t& b, ulonglong2 w, uint64_t q,
-                                               uint64_t q2) {
-        harvey_inv32(a, b, (uint32_t)w.x, (uint32_t)w.y, (uint32_t)q, (uint32_t)q2);
+                                               uint64_t m) {
+        harvey_inv32(a, b, (uint32_t)w.x, (uint32_t)w.y, (uint32_t)q, (uint32_t)m);
     }
     static __device__ __forceinline__ uint32_t mul(uint32_t x, uint64_t w, uint64_t wp,
                                                    uint64_t q) {
         return shoup_mul_lazy32(x, (uint32_t)w, (uint32_t)wp, (uint32_t)q);
     }
 };
+
+// Final correction of a transform's last stage: values in [0, B q) (B = 2m/q
+// for the forward, m/q for the inverse) brought into [0, out_mf q) by
+// conditional subtractions of (B/2) q, (B/4) q, ..., out_mf q.
+template <typename Wd, int B>
+__device__ __forceinline__ Wd to_out_range(Wd y, uint64_t q, uint32_t out_mf) {
+#pragma unroll
+    for (int k = B / 2; k >= 1; k >>= 1) {
+        if (out_mf <= (uint32_t)k) {
+            const Wd kq = (Wd)((uint64_t)k * q);
+            y = y >= kq ? y - kq : y;
+        }
+    }
+    return y;
+}
 
 struct TileCtx {
     const uint64_t* gin;   // this transform's input, element 0
@@ -138,8 +162,8 @@ enum { IO_SMEM = 0, IO_GLOBAL = 1 };
 // With NP > 1 the thread holds the same positions of NP polynomials (same
 // limb, same twiddles): every twiddle pair it loads serves NP butterflies.
 // Polynomial p's tile lives at sm + p * TE in shared memory.
-template <bool FWD, typename Wd, int LOG_R, int K, int P, int R, int SRC, int DST, int NP = 1,
-          bool ROW = false>
+template <bool FWD, typename Wd, int AR, int LOG_R, int K, int P, int R, int SRC, int DST,
+          int NP = 1, bool ROW = false>
 __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                           const LimbDev& lc, const TileCtx& c) {
     constexpr int RN = 1 << LOG_R;
@@ -194,7 +218,7 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         }
     }
 
-    const uint64_t q = lc.q, q2 = lc.two_q;
+    const uint64_t q = lc.q, qm = (uint64_t)Word<Wd, AR>::M * lc.q;
 #pragma unroll
     for (int kk = 0; kk < R; ++kk) {
         const int k = FWD ? kk : R - 1 - kk;
@@ -209,10 +233,10 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
                     if (reg0 & (1 << hb)) continue;
                     const int reg1 = reg0 | (1 << hb);
                     const Wd a = xs[pp][reg0], b = xs[pp][reg1];
-                    const Wd sum = a + b;              // [0, 4q)
-                    const Wd dif = a - b + (Wd)q2;     // (0, 4q)
-                    xs[pp][reg0] = Word<Wd>::mul(sum, lc.ninv, lc.ninv_p, q);
-                    xs[pp][reg1] = Word<Wd>::mul(dif, lc.ninv_w, lc.ninv_w_p, q);
+                    const Wd sum = a + b;              // [0, 2m)
+                    const Wd dif = a - b + (Wd)qm;     // (0, 2m)
+                    xs[pp][reg0] = Word<Wd, AR>::mul(sum, lc.ninv, lc.ninv_p, q);
+                    xs[pp][reg1] = Word<Wd, AR>::mul(dif, lc.ninv_w, lc.ninv_w_p, q);
                 }
             }
             continue;
@@ -229,21 +253,19 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp) {
                 if (FWD)
-                    Word<Wd>::fwd(xs[pp][reg0], xs[pp][reg1], w, q, q2);
+                    Word<Wd, AR>::fwd(xs[pp][reg0], xs[pp][reg1], w, q, qm);
                 else
-                    Word<Wd>::inv(xs[pp][reg0], xs[pp][reg1], w, q, q2);
+                    Word<Wd, AR>::inv(xs[pp][reg0], xs[pp][reg1], w, q, qm);
             }
         }
     }
-    if (c.last && c.out_mf == 1) {
+    if (c.last) {
+        constexpr int B = (FWD ? 2 : 1) * Word<Wd, AR>::M;
 #pragma unroll
         for (int pp = 0; pp < NP; ++pp) {
 #pragma unroll
-            for (int reg = 0; reg < RN; ++reg) {
-                Wd y = xs[pp][reg];
-                if (FWD) y = y >= (Wd)q2 ? y - (Wd)q2 : y;
-                xs[pp][reg] = y >= (Wd)q ? y - (Wd)q : y;
-            }
+            for (int reg = 0; reg < RN; ++reg)
+                xs[pp][reg] = to_out_range<Wd, B>(xs[pp][reg], q, c.out_mf);
         }
     }
 
@@ -303,7 +325,7 @@ __device__ __forceinline__ void smem_to_tile(const uint64_t* sm, const TileCtx& 
 // rounds; row passes do so at their low-stage end only (the forward's first
 // round, the inverse's last) and stage the high-stage end through shared
 // memory, where the round's thread map is strided.
-template <bool FWD, bool COLUMN, typename Wd, int LOG_R, int K, int I, int NP = 1>
+template <bool FWD, bool COLUMN, typename Wd, int AR, int LOG_R, int K, int I, int NP = 1>
 __device__ __forceinline__ void ntt_rounds(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                            const LimbDev& lc, const TileCtx& c) {
     using S = Sched<K, LOG_R>;
@@ -314,11 +336,11 @@ __device__ __forceinline__ void ntt_rounds(uint64_t* sm, const ulonglong2* __res
     constexpr bool direct_out = lastr && (COLUMN || !FWD);
     TileCtx cr = c;
     cr.last = c.last && lastr;
-    ntt_round<FWD, Wd, LOG_R, K, S::off(idx), S::size(idx), direct_in ? IO_GLOBAL : IO_SMEM,
+    ntt_round<FWD, Wd, AR, LOG_R, K, S::off(idx), S::size(idx), direct_in ? IO_GLOBAL : IO_SMEM,
               direct_out ? IO_GLOBAL : IO_SMEM, NP, !COLUMN>(sm, tw, lc, cr);
     if constexpr (!lastr) {
         __syncthreads();
-        ntt_rounds<FWD, COLUMN, Wd, LOG_R, K, I + 1, NP>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, Wd, AR, LOG_R, K, I + 1, NP>(sm, tw, lc, c);
     }
 }
 
@@ -337,9 +359,11 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
     }
     const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
     if (lc.narrow)
-        ntt_rounds<FWD, COLUMN, uint32_t, LOG_R, K, 0, NP>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, uint32_t, 0, LOG_R, K, 0, NP>(sm, tw, lc, c);
+    else if (lc.trunc)
+        ntt_rounds<FWD, COLUMN, uint64_t, 1, LOG_R, K, 0, NP>(sm, tw, lc, c);
     else
-        ntt_rounds<FWD, COLUMN, uint64_t, LOG_R, K, 0, NP>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, uint64_t, 0, LOG_R, K, 0, NP>(sm, tw, lc, c);
     if (staged_out) {
         __syncthreads();
         smem_to_tile<K, NP>(sm, c, TE);
@@ -454,7 +478,7 @@ __device__ __forceinline__ void smem16_to_tile(const uint64_t* sm, const TileCtx
 // One register round of the pipelined kernel: reads its elements from the
 // (swz16) tile in shared memory, writes them back there or, in the last
 // round of a coalesced end, straight to HBM.
-template <bool FWD, typename Wd, int LOG_R, int K, int P, int R, bool TO_GLOBAL>
+template <bool FWD, typename Wd, int AR, int LOG_R, int K, int P, int R, bool TO_GLOBAL>
 __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                            const LimbDev& lc, const TileCtx& c) {
     constexpr int RN = 1 << LOG_R;
@@ -496,7 +520,7 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
         x[reg] = (Wd)sm[swz16(lbase[u] + ((uint32_t)v << sshift))];
     }
 
-    const uint64_t q = lc.q, q2 = lc.two_q;
+    const uint64_t q = lc.q, qm = (uint64_t)Word<Wd, AR>::M * lc.q;
 #pragma unroll
     for (int kk = 0; kk < R; ++kk) {
         const int k = FWD ? kk : R - 1 - kk;
@@ -508,9 +532,9 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
                 const int reg1 = reg0 | (1 << hb);
                 const Wd a = x[reg0], b = x[reg1];
                 const Wd sum = a + b;
-                const Wd dif = a - b + (Wd)q2;
-                x[reg0] = Word<Wd>::mul(sum, lc.ninv, lc.ninv_p, q);
-                x[reg1] = Word<Wd>::mul(dif, lc.ninv_w, lc.ninv_w_p, q);
+                const Wd dif = a - b + (Wd)qm;
+                x[reg0] = Word<Wd, AR>::mul(sum, lc.ninv, lc.ninv_p, q);
+                x[reg1] = Word<Wd, AR>::mul(dif, lc.ninv_w, lc.ninv_w_p, q);
             }
             continue;
         }
@@ -521,18 +545,15 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
             const int u = reg0 & (U - 1), v0 = reg0 >> (LOG_R - R);
             const ulonglong2 w = wt[u][(1 << k) - 1 + (v0 >> (R - k))];
             if (FWD)
-                Word<Wd>::fwd(x[reg0], x[reg1], w, q, q2);
+                Word<Wd, AR>::fwd(x[reg0], x[reg1], w, q, qm);
             else
-                Word<Wd>::inv(x[reg0], x[reg1], w, q, q2);
+                Word<Wd, AR>::inv(x[reg0], x[reg1], w, q, qm);
         }
     }
-    if (c.last && c.out_mf == 1) {
+    if (c.last) {
+        constexpr int B = (FWD ? 2 : 1) * Word<Wd, AR>::M;
 #pragma unroll
-        for (int reg = 0; reg < RN; ++reg) {
-            Wd y = x[reg];
-            if (FWD) y = y >= (Wd)q2 ? y - (Wd)q2 : y;
-            x[reg] = y >= (Wd)q ? y - (Wd)q : y;
-        }
+        for (int reg = 0; reg < RN; ++reg) x[reg] = to_out_range<Wd, B>(x[reg], q, c.out_mf);
     }
     if (TO_GLOBAL) {
         const int gshift = ELO + c.w;
@@ -552,7 +573,7 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
     }
 }
 
-template <bool FWD, bool COLUMN, typename Wd, int LOG_R, int K, int I>
+template <bool FWD, bool COLUMN, typename Wd, int AR, int LOG_R, int K, int I>
 __device__ __forceinline__ void pipe_rounds(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                             const LimbDev& lc, const TileCtx& c) {
     using S = Sched<K, LOG_R>;
@@ -561,11 +582,11 @@ __device__ __forceinline__ void pipe_rounds(uint64_t* sm, const ulonglong2* __re
     constexpr bool lastr = I == NR - 1;
     TileCtx cr = c;
     cr.last = c.last && lastr;
-    pipe_round<FWD, Wd, LOG_R, K, S::off(idx), S::size(idx), lastr && (COLUMN || !FWD)>(sm, tw,
-                                                                                       lc, cr);
+    pipe_round<FWD, Wd, AR, LOG_R, K, S::off(idx), S::size(idx), lastr && (COLUMN || !FWD)>(
+        sm, tw, lc, cr);
     if constexpr (!lastr) {
         __syncthreads();
-        pipe_rounds<FWD, COLUMN, Wd, LOG_R, K, I + 1>(sm, tw, lc, c);
+        pipe_rounds<FWD, COLUMN, Wd, AR, LOG_R, K, I + 1>(sm, tw, lc, c);
     }
 }
 
@@ -600,9 +621,11 @@ __global__ void __launch_bounds__(256, 2) ntt_pipe_kernel(PassArgs a) {
         const LimbDev lc = a.limbs[id.limb];
         const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
         if (lc.narrow)
-            pipe_rounds<FWD, COLUMN, uint32_t, LOG_R, K, 0>(buf, tw, lc, c);
+            pipe_rounds<FWD, COLUMN, uint32_t, 0, LOG_R, K, 0>(buf, tw, lc, c);
+        else if (lc.trunc)
+            pipe_rounds<FWD, COLUMN, uint64_t, 1, LOG_R, K, 0>(buf, tw, lc, c);
         else
-            pipe_rounds<FWD, COLUMN, uint64_t, LOG_R, K, 0>(buf, tw, lc, c);
+            pipe_rounds<FWD, COLUMN, uint64_t, 0, LOG_R, K, 0>(buf, tw, lc, c);
         if (!COLUMN && FWD) {
             __syncthreads();
             smem16_to_tile<K>(buf, c, TE);

@@ -112,6 +112,8 @@ static void fill_limb(uint64_t N, int logN, uint64_t q, uint64_t psi, ulonglong2
     ld->ninv_w = ninv_w;
     ld->ninv_w_p = shoup(ninv_w, q, narrow);
     ld->narrow = narrow ? 1u : 0u;
+    ld->trunc = (!narrow && q < (1ull << 61)) ? 1u : 0u;
+    ld->pad_ = 0;
     int Q = 0;
     while (Q < 64 && (q >> Q)) ++Q;   // bit length; q is an odd prime, so q > 2^(Q-1)
     ld->barrett_qm1 = (uint32_t)(Q - 1);

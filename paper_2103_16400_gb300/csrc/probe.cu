@@ -10,7 +10,8 @@
 //
 // hx_probe_butterfly_rate: the same grid runs Harvey forward or inverse
 // butterflies on register-resident data (no memory traffic), giving the
-// arithmetic ceiling of each Shoup-product variant of the butterfly code.
+// arithmetic ceiling of each Shoup-product variant of the butterfly code
+// (variants 0-2: exact quotient, lazy bound 2q; 3: truncated quotient, 4q).
 #include <atomic>
 
 #include "hx_internal.h"
@@ -63,10 +64,11 @@ __global__ void __launch_bounds__(256) butterfly_probe_kernel(uint32_t iters, ui
 #pragma unroll
         for (int i = 0; i < 8; i += 2) {
             if constexpr (sizeof(Wd) == 8) {
+                const uint64_t m = (V == 3 ? 4 : 2) * q;
                 if (INV)
-                    harvey_inv64<V>(x[i], x[i + 1], w, wp, q, 2 * q);
+                    harvey_inv64<V>(x[i], x[i + 1], w, wp, q, m);
                 else
-                    harvey_fwd64<V>(x[i], x[i + 1], w, wp, q, 2 * q);
+                    harvey_fwd64<V>(x[i], x[i + 1], w, wp, q, m);
             } else {
                 if (INV)
                     harvey_inv32(x[i], x[i + 1], (uint32_t)w, (uint32_t)wp, (uint32_t)q,
@@ -160,15 +162,18 @@ extern "C" int hx_probe_butterfly_rate(uint32_t variant, uint32_t iters, uint64_
     if (!butterflies_per_s) return HX_ERR_NULL;
     const uint32_t v = variant & 15u;
     const bool inv = (variant >> 4) & 1u;
-    if (iters == 0 || q < 3 || q >= (1ull << 62) || v > 2) return HX_ERR_ARG;
+    if (iters == 0 || q < 3 || q >= (1ull << 62) || v > 3) return HX_ERR_ARG;
+    if (v == 3 && q >= (1ull << 61)) return HX_ERR_ARG;
     const int blocks = sm_count() * 8;
     uint64_t* sink = nullptr;
     if (cudaMalloc(&sink, blocks * sizeof(uint64_t)) != cudaSuccess) return HX_ERR_NOMEM;
     const uint64_t w = q / 3 + 1;
     const bool narrow = q < (1ull << 30);
     const uint64_t wp = narrow ? ((w << 32) / q) : (uint64_t)(((unsigned __int128)w << 64) / q);
-    BflyKernel k = v == 0 ? bfly_kernel<0>(narrow, inv)
-                          : v == 1 ? bfly_kernel<1>(narrow, inv) : bfly_kernel<2>(narrow, inv);
+    BflyKernel k = v == 0   ? bfly_kernel<0>(narrow, inv)
+                   : v == 1 ? bfly_kernel<1>(narrow, inv)
+                   : v == 2 ? bfly_kernel<2>(narrow, inv)
+                            : bfly_kernel<3>(narrow, inv);
     cudaStream_t st = (cudaStream_t)stream;
     float t = time_probe(st, [&](uint32_t it) { k<<<blocks, 256, 0, st>>>(it, q, w, wp, sink); },
                          iters);

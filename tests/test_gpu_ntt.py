@@ -111,6 +111,41 @@ def test_extreme_inputs(hexlib):
     assert (gpu_forward(plan, delta)[0] == 1).all()          # NTT(1) = (1, ..., 1)
 
 
+def _largest_ntt_prime_below(bound, two_n):
+    q = (bound - 1) // two_n * two_n + 1
+    while not W.is_prime(q):
+        q -= two_n
+    return q
+
+
+def test_truncated_quotient_boundary(hexlib):
+    """64-bit limbs with q < 2^61 take the truncated-quotient Shoup product
+    (lazy bound 4q), q >= 2^61 the exact one (2q): the largest NTT prime below
+    2^61 and the smallest above, with every coefficient at the top of the
+    allowed input range and with random inputs, forward and inverse, canonical
+    and lazy outputs."""
+    N = 1 << 13
+    qs = [_largest_ntt_prime_below(1 << 61, 2 * N), W.ntt_primes(62, 2 * N, 1)[0],
+          _largest_ntt_prime_below(1 << 50, 2 * N), MIXED3[2]]
+    assert qs[0] < (1 << 61) <= qs[1]
+    plan = Plan(N, qs)
+    top = np.stack([np.full(N, 4 * q - 1, dtype=np.uint64) for q in qs])[None]
+    rnd = W.poly_batch(W.SEED_BASE + 520, 1, 3, qs, N)
+    for x, in_mf in ((top, 4), (rnd, 1)):
+        exp = oracle.ntt_forward(x, qs)
+        got, _ = gpu_forward(plan, x, in_mf=in_mf, out_mf=1)
+        np.testing.assert_array_equal(got, exp)
+        lazy, _ = gpu_forward(plan, x, in_mf=in_mf, out_mf=4)
+        assert_lazy(lazy, exp, qs, 4)
+    top2 = np.stack([np.full(N, 2 * q - 1, dtype=np.uint64) for q in qs])[None]
+    for y, in_mf in ((top2, 2), (oracle.ntt_forward(rnd, qs), 1)):
+        exp = oracle.ntt_inverse(y, qs)
+        got, _ = gpu_inverse(plan, y, in_mf=in_mf, out_mf=1)
+        np.testing.assert_array_equal(got, exp)
+        lazy, _ = gpu_inverse(plan, y, in_mf=in_mf, out_mf=2)
+        assert_lazy(lazy, exp, qs, 2)
+
+
 def test_many_polys_and_limbs(hexlib):
     N = 1 << 10
     qs = W.mixed_width_primes(7)
