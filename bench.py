@@ -67,13 +67,22 @@ def device_sets(sets):
     return [(to_device(np.concatenate(ins)), to_device(np.concatenate(es))) for ins, es in sets]
 
 
-#: IMAD-pipe issue slots of one exact Shoup butterfly, in units of one 32-bit
-#: mad.lo (the probes measure mad.hi and mad.wide at half that rate or less):
-#: 64-bit words -- high word of W'X from four partial products (one high
-#: half, three full products: 1*2 + 3*(1+2) = 11), remainder W X - Q q mod
-#: 2^64 from two full low products and four low halves (2*(1+2) + 4 = 10);
-#: 32-bit words -- one high half and two low halves (2 + 1 + 1 = 4).
-SLOTS_WIDE, SLOTS_NARROW = 21, 4
+#: IMAD-pipe issue slots of one Shoup butterfly as the kernels compute it, in
+#: units of one 32-bit mad.lo (the probes measure mad.hi at half that rate
+#: and mad.wide at under half): a full 32x32-bit product counts 1 + 2.
+#: 64-bit words, q < 2^61 (truncated quotient) -- high word of W'X from three
+#: partial products (two high halves, one full product: 2*2 + 3 = 7), plus
+#: the remainder W X - Q q mod 2^64 from two full low products and four low
+#: halves (2*3 + 4 = 10): 17.  64-bit words, q >= 2^61 (exact quotient) --
+#: high word from four partial products (2 + 3*3 = 11) plus the remainder:
+#: 21.  32-bit words -- one high half and two low halves (2 + 1 + 1 = 4).
+SLOTS_WIDE_TRUNC, SLOTS_WIDE, SLOTS_NARROW = 17, 21, 4
+
+
+def slots_per_butterfly(q):
+    if q < (1 << 30):
+        return SLOTS_NARROW
+    return SLOTS_WIDE_TRUNC if q < (1 << 61) else SLOTS_WIDE
 
 
 def imad_slots_per_transform(N, moduli):
@@ -81,7 +90,7 @@ def imad_slots_per_transform(N, moduli):
     butterflies, each one Shoup product."""
     logn = N.bit_length() - 1
     bf = N // 2 * logn
-    return [bf * (SLOTS_NARROW if q < (1 << 30) else SLOTS_WIDE) for q in moduli]
+    return [bf * slots_per_butterfly(q) for q in moduli]
 
 
 class HexStep:
@@ -440,7 +449,8 @@ def run_case(args):
     plan = capi.Plan(N, wl.moduli)
     if args.tuned and args.case in ("fwd", "inv"):
         from paper_2103_16400_gb300 import tune as hx_tune
-        t = hx_tune.tune(plan, P, direction=plan.FORWARD if args.case == "fwd" else plan.INVERSE)
+        t = hx_tune.tune(plan, P, direction=plan.FORWARD if args.case == "fwd" else plan.INVERSE,
+                         verbose=bool(os.environ.get("HX_TUNE_VERBOSE")))
         out["schedule"] = t["forward" if args.case == "fwd" else "inverse"]
     s = W.scalars(wl.seed, 20, wl.moduli)
     st = torch.cuda.current_stream()

@@ -113,7 +113,9 @@ int hx_plan_info(hx_plan_t plan, uint64_t* N, uint32_t* n_limbs, uint64_t* devic
  * pass covers stages [s0, s0 + K) of the log2 N stages; a tile is
  * 2^logGb x 2^K x 2^logGc elements (top-index values x stage bits x
  * low-index values); 2^logR elements per thread; pipe = 1 selects the
- * persistent double-buffered kernel; np (1 or 2) is the number of
+ * persistent double-buffered kernel, pipe = 2 the per-tile kernel that first
+ * copies the tile's twiddle pairs into shared memory (pipe = 0: per-tile,
+ * twiddles read through the read-only cache); np (1 or 2) is the number of
  * polynomials each thread transforms with one set of twiddle registers.
  * hx_plan_set_schedule returns HX_ERR_ARG for a schedule the library cannot
  * run (stages not covering [0, log2 N), a kernel not in the menu, tile too

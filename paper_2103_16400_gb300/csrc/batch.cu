@@ -71,6 +71,7 @@ __device__ __forceinline__ void rag_tile(uint64_t* sm, const RagTile& d) {
     c.L = L;
     c.s0 = s0;
     c.logGc = logGc;
+    c.logGb = logGb;
     c.w = w;
     c.nthreads = (1u << logTE) >> LOG_R;
     c.out_mf = d.out_mf;

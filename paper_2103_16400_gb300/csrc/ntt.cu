@@ -19,9 +19,16 @@ namespace hx {
 
 static PassKernel pick(bool fwd, const PassCfg& p) {
     const bool column = p.logGc > 0;
-    if (p.pipe)
+    if (p.pipe == 1)
         return p.np != 1 ? nullptr
                          : fwd ? pick_pipe_f(column, p.logR, p.K) : pick_pipe_i(column, p.logR, p.K);
+    if (p.pipe == 2) {
+        if (p.np == 2)
+            return fwd ? pick_tws_f2(column, p.logR, p.K) : pick_tws_i2(column, p.logR, p.K);
+        if (p.np == 1)
+            return fwd ? pick_tws_f1(column, p.logR, p.K) : pick_tws_i1(column, p.logR, p.K);
+        return nullptr;
+    }
     if (p.np == 2)
         return fwd ? pick_plain_f2(column, p.logR, p.K) : pick_plain_i2(column, p.logR, p.K);
     if (p.np == 1)
@@ -29,8 +36,19 @@ static PassKernel pick(bool fwd, const PassCfg& p) {
     return nullptr;
 }
 
+// Dynamic shared memory of one block of a pass: the persistent kernel's two
+// tile buffers; the per-tile kernels' NP padded data tiles, plus the staged
+// twiddle pairs in mode 2.
+static size_t pass_smem(const PassCfg& p) {
+    const int logTE = p.logGb + p.K + p.logGc;
+    if (p.pipe == 1) return (size_t)16 << logTE;
+    size_t b = (size_t)8 * p.np * padded(1u << logTE);
+    if (p.pipe == 2) b += 16 * (size_t)staged_twiddles(p.logGb, p.K);
+    return b;
+}
+
 static bool pass_ok(int L, const PassCfg& p) {
-    if (p.pipe != 0 && p.pipe != 1) return false;
+    if (p.pipe < 0 || p.pipe > 2) return false;
     if (!pick(true, p) || !pick(false, p)) return false;
     const int w = L - p.s0 - p.K;
     if (w < 0 || p.s0 < 0) return false;
@@ -40,10 +58,8 @@ static bool pass_ok(int L, const PassCfg& p) {
     if (w > 0 && p.logGb != 0) return false;
     const int logTE = p.logGb + p.K + p.logGc;
     const int logT = logTE - p.logR;
-    if (logT < 5 || logT > (p.pipe ? 8 : 9)) return false;      // 32 .. 256 / 512 threads
-    const size_t smem = p.pipe ? (size_t)16 << logTE
-                                    : (size_t)8 * p.np * padded(1u << logTE);
-    if (smem > 192 * 1024) return false;
+    if (logT < 5 || logT > (p.pipe == 1 ? 8 : 9)) return false;   // 32 .. 256 / 512 threads
+    if (pass_smem(p) > 192 * 1024) return false;
     return true;
 }
 
@@ -100,8 +116,7 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
         const int logTE = p.logGb + p.K + p.logGc;
         const uint32_t tiles = 1u << (L - logTE);
         const uint32_t threads = 1u << (logTE - p.logR);
-        const size_t smem = p.pipe ? (size_t)16 << logTE
-                                    : (size_t)8 * p.np * padded(1u << logTE);
+        const size_t smem = pass_smem(p);
         PassKernel k = pick(forward, p);
         if (!k) return cudaErrorInvalidConfiguration;
         if (smem > 48 * 1024) {
@@ -110,7 +125,7 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
         }
-        if (p.pipe) {
+        if (p.pipe == 1) {
             int sms = 0;
             const int per_sm = resident_blocks(k, threads, smem, &sms);
             const uint64_t total = (uint64_t)tiles * n_polys * plan->n_limbs;

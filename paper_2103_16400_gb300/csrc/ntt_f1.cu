@@ -5,11 +5,11 @@
 namespace hx {
 
 PassKernel pick_plain_f1(bool column, int logR, int K) {
-    return menu<true, 1, false>(column, logR, K);
+    return menu<true, 1, 0>(column, logR, K);
 }
 
 PassKernel pick_pipe_f(bool column, int logR, int K) {
-    return menu<true, 1, true>(column, logR, K);
+    return menu<true, 1, 1>(column, logR, K);
 }
 
 }  // namespace hx

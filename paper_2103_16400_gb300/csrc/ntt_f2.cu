@@ -5,7 +5,7 @@
 namespace hx {
 
 PassKernel pick_plain_f2(bool column, int logR, int K) {
-    return menu<true, 2, false>(column, logR, K);
+    return menu<true, 2, 0>(column, logR, K);
 }
 
 }  // namespace hx

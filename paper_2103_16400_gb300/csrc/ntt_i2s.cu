@@ -1,0 +1,11 @@
+// Instantiations of the inverse (Gentleman-Sande / Harvey) pass kernels with 2 polynomial(s) per
+// thread and the tile's twiddles staged in shared memory.
+#include "ntt_inst.cuh"
+
+namespace hx {
+
+PassKernel pick_tws_i2(bool column, int logR, int K) {
+    return menu<false, 2, 2>(column, logR, K);
+}
+
+}  // namespace hx

@@ -128,12 +128,26 @@ __device__ __forceinline__ Wd to_out_range(Wd y, uint64_t q, uint32_t out_mf) {
     return y;
 }
 
+// 16-byte asynchronous copies global -> shared (cp.async, bypassing registers).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 struct TileCtx {
     const uint64_t* gin;   // this transform's input, element 0
     uint64_t* gout;        // this transform's output, element 0
     uint64_t b_base;       // first top-index value of the tile
     uint64_t c_base;       // first low-index value of the tile
     int L, s0, logGc, w;   // w = L - s0 - K: low bits below the pass's stages
+    int logGb = 0;         // log2 of top-index values per tile
     uint32_t nthreads;
     uint32_t out_mf;
     bool last;
@@ -162,8 +176,11 @@ enum { IO_SMEM = 0, IO_GLOBAL = 1 };
 // With NP > 1 the thread holds the same positions of NP polynomials (same
 // limb, same twiddles): every twiddle pair it loads serves NP butterflies.
 // Polynomial p's tile lives at sm + p * TE in shared memory.
+// With TWS the twiddles come from the tile's staged copy in shared memory
+// (stage_twiddles), `tw` pointing at it; WAIT_TW makes this round wait for
+// that copy after issuing its own loads.
 template <bool FWD, typename Wd, int AR, int LOG_R, int K, int P, int R, int SRC, int DST,
-          int NP = 1, bool ROW = false>
+          int NP = 1, bool ROW = false, bool TWS = false, bool WAIT_TW = false>
 __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                           const LimbDev& lc, const TileCtx& c) {
     constexpr int RN = 1 << LOG_R;
@@ -172,7 +189,7 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
     const uint32_t TEP = padded(c.nthreads << LOG_R);
     Wd xs[NP][RN];
     uint64_t pfx[U];
-    uint32_t lbase[U];
+    uint32_t lbase[U], hiu[U];
     const uint32_t cmask = (1u << c.logGc) - 1;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -185,6 +202,7 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         const uint32_t bl = t2 >> P;
         lbase[u] = (bl << (K + c.logGc)) | (ehi << (K - P + c.logGc)) | (elo << c.logGc) | cl;
         pfx[u] = ((c.b_base + bl) << P) | ehi;
+        hiu[u] = (bl << P) | ehi;
     }
     const int sshift = ROW ? ELO : ELO + c.logGc;   // v stride in the tile
     const int gshift = ELO + c.w;                   // v stride in global memory
@@ -217,6 +235,10 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
             }
         }
     }
+    if constexpr (WAIT_TW) {
+        cp_async_wait<0>();
+        __syncthreads();
+    }
 
     const uint64_t q = lc.q, qm = (uint64_t)Word<Wd, AR>::M * lc.q;
 #pragma unroll
@@ -243,13 +265,16 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         }
         const ulonglong2* tb[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) tb[u] = tw + ((1ull << s) + (pfx[u] << k));
+        for (int u = 0; u < U; ++u)
+            tb[u] = TWS ? tw + ((((1u << (P + k)) - 1) << c.logGb) + hiu[u])
+                        : tw + ((1ull << s) + (pfx[u] << k));
 #pragma unroll
         for (int reg0 = 0; reg0 < RN; ++reg0) {
             if (reg0 & (1 << hb)) continue;
             const int reg1 = reg0 | (1 << hb);
             const int u = reg0 & (U - 1), v0 = reg0 >> (LOG_R - R);
-            const ulonglong2 w = __ldg(tb[u] + (v0 >> (R - k)));
+            const ulonglong2 w = TWS ? tb[u][(uint32_t)(v0 >> (R - k)) << (c.logGb + P)]
+                                     : __ldg(tb[u] + (v0 >> (R - k)));
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp) {
                 if (FWD)
@@ -325,7 +350,8 @@ __device__ __forceinline__ void smem_to_tile(const uint64_t* sm, const TileCtx& 
 // rounds; row passes do so at their low-stage end only (the forward's first
 // round, the inverse's last) and stage the high-stage end through shared
 // memory, where the round's thread map is strided.
-template <bool FWD, bool COLUMN, typename Wd, int AR, int LOG_R, int K, int I, int NP = 1>
+template <bool FWD, bool COLUMN, typename Wd, int AR, int LOG_R, int K, int I, int NP = 1,
+          bool TWS = false>
 __device__ __forceinline__ void ntt_rounds(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                            const LimbDev& lc, const TileCtx& c) {
     using S = Sched<K, LOG_R>;
@@ -337,33 +363,76 @@ __device__ __forceinline__ void ntt_rounds(uint64_t* sm, const ulonglong2* __res
     TileCtx cr = c;
     cr.last = c.last && lastr;
     ntt_round<FWD, Wd, AR, LOG_R, K, S::off(idx), S::size(idx), direct_in ? IO_GLOBAL : IO_SMEM,
-              direct_out ? IO_GLOBAL : IO_SMEM, NP, !COLUMN>(sm, tw, lc, cr);
+              direct_out ? IO_GLOBAL : IO_SMEM, NP, !COLUMN, TWS, TWS && direct_in>(sm, tw, lc,
+                                                                                 cr);
     if constexpr (!lastr) {
         __syncthreads();
-        ntt_rounds<FWD, COLUMN, Wd, AR, LOG_R, K, I + 1, NP>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, Wd, AR, LOG_R, K, I + 1, NP, TWS>(sm, tw, lc, c);
     }
+}
+
+// Copies the twiddle pairs of every stage of the tile into shared memory
+// (asynchronously; the caller commits and waits).  Stage p of the pass uses
+// table entries 2^(s0+p) + (b << p) + e for the tile's 2^logGb top-index
+// values b and e < 2^p: 2^(logGb+p) consecutive pairs, stored from
+// 2^logGb (2^p - 1) on.  Within a stage, entry i = (h << k) + j -- k the
+// stage's position in its register round (round offset P), h = (b_local << P)
+// | e_hi the group's index -- goes to (j << (logGb + P)) + h, so that for
+// each j the groups of consecutive threads read consecutive pairs.
+template <int K, int LOG_R>
+__device__ __forceinline__ void stage_twiddles(ulonglong2* tws, const ulonglong2* __restrict__ tw,
+                                               const TileCtx& c) {
+    using S = Sched<K, LOG_R>;
+    const int lgb = c.logGb;
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+        int P = 0;
+#pragma unroll
+        for (int r = 0; r < S::NR; ++r)
+            if (p >= S::off(r)) P = S::off(r);
+        const int k = p - P;
+        const uint32_t cnt = 1u << (lgb + p);
+        const ulonglong2* src = tw + ((1ull << (c.s0 + p)) + (c.b_base << p));
+        ulonglong2* dst = tws + (((1u << p) - 1) << lgb);
+        for (uint32_t i = threadIdx.x; i < cnt; i += c.nthreads)
+            cp_async16(dst + ((i & ((1u << k) - 1)) << (lgb + P)) + (i >> k), src + i);
+    }
+}
+
+// Pairs in a tile's staged twiddle copy: 2^logGb (2^K - 1).
+__host__ __device__ constexpr uint32_t staged_twiddles(int logGb, int K) {
+    return ((1u << K) - 1) << logGb;
 }
 
 // One tile of one pass (for each of NP polynomials), by the whole block
 // (TE >> LOG_R threads): stage in through shared memory where the first
 // round's map is strided, run the rounds, stage out where the last round's
 // map is strided.
-template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1>
+// With TWS the tile's twiddles are first copied to shared memory after the
+// NP data tiles (stage_twiddles), overlapping the first data loads.
+template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false>
 __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, const LimbDev& lc,
                                              uint32_t TE) {
     constexpr bool staged_in = !COLUMN && !FWD;
     constexpr bool staged_out = !COLUMN && FWD;
+    const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
+    if constexpr (TWS) {
+        ulonglong2* tws = reinterpret_cast<ulonglong2*>(sm + NP * padded(TE));
+        stage_twiddles<K, LOG_R>(tws, tw, c);
+        cp_async_commit();
+        tw = tws;
+    }
     if (staged_in) {
         tile_to_smem<K, NP>(sm, c, TE);
+        if constexpr (TWS) cp_async_wait<0>();
         __syncthreads();
     }
-    const ulonglong2* tw = FWD ? lc.fwd : lc.inv;
     if (lc.narrow)
-        ntt_rounds<FWD, COLUMN, uint32_t, 0, LOG_R, K, 0, NP>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, uint32_t, 0, LOG_R, K, 0, NP, TWS>(sm, tw, lc, c);
     else if (lc.trunc)
-        ntt_rounds<FWD, COLUMN, uint64_t, 1, LOG_R, K, 0, NP>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, uint64_t, 1, LOG_R, K, 0, NP, TWS>(sm, tw, lc, c);
     else
-        ntt_rounds<FWD, COLUMN, uint64_t, 0, LOG_R, K, 0, NP>(sm, tw, lc, c);
+        ntt_rounds<FWD, COLUMN, uint64_t, 0, LOG_R, K, 0, NP, TWS>(sm, tw, lc, c);
     if (staged_out) {
         __syncthreads();
         smem_to_tile<K, NP>(sm, c, TE);
@@ -371,7 +440,7 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
 }
 
 // One block per (tile, group of NP polynomials, limb).
-template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1>
+template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false>
 __global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
     extern __shared__ uint64_t sm[];
     const uint32_t limb = blockIdx.y;
@@ -391,13 +460,14 @@ __global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
     c.L = a.L;
     c.s0 = a.s0;
     c.logGc = a.logGc;
+    c.logGb = a.logGb;
     c.w = a.L - a.s0 - K;
     c.nthreads = TE >> LOG_R;
     c.out_mf = a.out_mf;
     c.last = a.last != 0;
     c.poly_stride = (uint64_t)a.n_limbs << a.L;
     c.np_valid = min((uint32_t)NP, a.n_polys - poly);
-    process_tile<FWD, COLUMN, LOG_R, K, NP>(sm, c, lc, TE);
+    process_tile<FWD, COLUMN, LOG_R, K, NP, TWS>(sm, c, lc, TE);
 }
 
 // ---------------------------------------------------------------------------
@@ -405,8 +475,8 @@ __global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
 // blockIdx.x, blockIdx.x + gridDim.x, ...; while it transforms tile t out of
 // one shared-memory buffer, the next tile streams into the other buffer with
 // cp.async (16-byte asynchronous copies that bypass the registers), so HBM
-// latency hides behind the butterflies even at two blocks per SM.  Each
-// round's twiddle pairs are all requested before its butterflies start.
+// latency hides behind the butterflies even at two blocks per SM; the next
+// tile's twiddle lines are requested into L1 at the same time.
 // Tiles are numbered (limb, tile, polynomial) with the polynomial fastest, so
 // blocks that run together share one limb's twiddles in L1/L2.
 // ---------------------------------------------------------------------------
@@ -416,17 +486,6 @@ __global__ void __launch_bounds__(512) ntt_pass_kernel(PassArgs a) {
 // schedules used here sees at most 2-way bank conflicts.
 __device__ __forceinline__ uint32_t swz16(uint32_t l) { return l ^ (((l >> 4) & 7u) << 1); }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 struct TileId {
     uint32_t limb, poly, tile;
@@ -453,6 +512,7 @@ __device__ __forceinline__ void tile_ctx(const TileId& id, const PassArgs& a, Ti
     c.L = a.L;
     c.s0 = a.s0;
     c.logGc = a.logGc;
+    c.logGb = a.logGb;
     c.w = a.L - a.s0 - K;
     c.out_mf = a.out_mf;
     c.last = a.last != 0;
@@ -463,6 +523,20 @@ __device__ __forceinline__ void tile_prefetch(uint64_t* dst, const TileCtx& c, u
     for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
         const uint32_t l = 2 * i;
         cp_async16(dst + swz16(l), c.gin + tile_gidx<K>(l, c));
+    }
+}
+
+// Asks L1 for the 128-byte lines of the twiddle pairs a tile will read (stage
+// p of the pass: 2^(logGb+p) pairs from entry 2^(s0+p) + (b << p)), so that
+// the tile's rounds find them there.
+template <int K>
+__device__ __forceinline__ void twiddle_prefetch_l1(const ulonglong2* tw, const TileCtx& c) {
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+        const ulonglong2* src = tw + ((1ull << (c.s0 + p)) + (c.b_base << p));
+        const uint32_t cnt = 1u << (c.logGb + p);
+        for (uint32_t i = threadIdx.x * 8; i < cnt; i += c.nthreads * 8)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(src + i));
     }
 }
 
@@ -484,7 +558,6 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
     constexpr int RN = 1 << LOG_R;
     constexpr int U = 1 << (LOG_R - R);
     constexpr int ELO = K - P - R;
-    constexpr int NTW = (1 << R) - 1;   // twiddles per group in this round
     Wd x[RN];
     uint64_t pfx[U];
     uint32_t lbase[U];
@@ -500,18 +573,6 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
         const uint32_t bl = t2 >> P;
         lbase[u] = (bl << (K + c.logGc)) | (ehi << (K - P + c.logGc)) | (elo << c.logGc) | cl;
         pfx[u] = ((c.b_base + bl) << P) | ehi;
-    }
-    // every twiddle of the round first: sub-stage k of group u needs entries
-    // 2^s + (pfx << k) + j, j < 2^k
-    ulonglong2 wt[U][NTW];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const ulonglong2* tb = tw + ((1ull << (c.s0 + P + k)) + (pfx[u] << k));
-#pragma unroll
-            for (int j = 0; j < (1 << k); ++j) wt[u][(1 << k) - 1 + j] = __ldg(tb + j);
-        }
     }
     const int sshift = ELO + c.logGc;
 #pragma unroll
@@ -538,12 +599,15 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
             }
             continue;
         }
+        const ulonglong2* tb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) tb[u] = tw + ((1ull << (c.s0 + P + k)) + (pfx[u] << k));
 #pragma unroll
         for (int reg0 = 0; reg0 < RN; ++reg0) {
             if (reg0 & (1 << hb)) continue;
             const int reg1 = reg0 | (1 << hb);
             const int u = reg0 & (U - 1), v0 = reg0 >> (LOG_R - R);
-            const ulonglong2 w = wt[u][(1 << k) - 1 + (v0 >> (R - k))];
+            const ulonglong2 w = __ldg(tb[u] + (v0 >> (R - k)));
             if (FWD)
                 Word<Wd, AR>::fwd(x[reg0], x[reg1], w, q, qm);
             else
@@ -591,7 +655,7 @@ __device__ __forceinline__ void pipe_rounds(uint64_t* sm, const ulonglong2* __re
 }
 
 template <bool FWD, bool COLUMN, int LOG_R, int K>
-__global__ void __launch_bounds__(256, 2) ntt_pipe_kernel(PassArgs a) {
+__global__ void __launch_bounds__(256, LOG_R == 3 ? 4 : 2) ntt_pipe_kernel(PassArgs a) {
     extern __shared__ uint64_t sm[];
     const int logTE = a.logGb + K + a.logGc;
     const uint32_t TE = 1u << logTE;
@@ -610,8 +674,10 @@ __global__ void __launch_bounds__(256, 2) ntt_pipe_kernel(PassArgs a) {
         if (tn < total) {
             TileCtx cn;
             cn.nthreads = c.nthreads;
-            tile_ctx<K>(decode_tile(tn, a, tiles), a, cn);
+            const TileId idn = decode_tile(tn, a, tiles);
+            tile_ctx<K>(idn, a, cn);
             tile_prefetch<K>(sm + ((i + 1) & 1) * TE, cn, TE);
+            twiddle_prefetch_l1<K>(FWD ? a.limbs[idn.limb].fwd : a.limbs[idn.limb].inv, cn);
         }
         cp_async_commit();
         cp_async_wait<1>();
@@ -646,5 +712,10 @@ PassKernel pick_plain_i1(bool column, int logR, int K);
 PassKernel pick_plain_i2(bool column, int logR, int K);
 PassKernel pick_pipe_f(bool column, int logR, int K);
 PassKernel pick_pipe_i(bool column, int logR, int K);
+// ntt_f1s.cu, ntt_f2s.cu, ntt_i1s.cu, ntt_i2s.cu: plain kernels with staged twiddles
+PassKernel pick_tws_f1(bool column, int logR, int K);
+PassKernel pick_tws_f2(bool column, int logR, int K);
+PassKernel pick_tws_i1(bool column, int logR, int K);
+PassKernel pick_tws_i2(bool column, int logR, int K);
 
 }  // namespace hx

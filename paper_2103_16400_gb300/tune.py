@@ -3,10 +3,14 @@
 The paper leaves the choice between its kernel variants to fixed CPUID rules
 and names choosing "via a small number of trials" as future work (Section
 3.2).  Here the trials are the schedule: how the log2 N stages split into
-passes, the tile shape of each pass, elements per thread, and whether a pass
-runs the persistent double-buffered kernel.  Every schedule computes the same
-result; `tune()` times each candidate's forward and inverse transform on the
-caller's plan and batch size with CUDA events and keeps the fastest.
+passes, the tile shape of each pass, elements per thread, and which kernel
+a pass runs (per-tile, persistent double-buffered, or per-tile with staged
+twiddles).  Every schedule computes the same result; `tune()` times
+candidates of the forward and of the inverse transform on the caller's plan
+and batch size with CUDA events and keeps the fastest of each: every
+single-pass schedule, and per split of the stages a coordinate search over
+the first pass, then the second (the passes are separate launches, so their
+times add).
 Winners are cached in a JSON file keyed by GPU name, N, limb-width mix and
 batch size.
 """
@@ -14,6 +18,7 @@ from __future__ import annotations
 
 import json
 import os
+import sys
 import threading
 from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 
@@ -26,26 +31,38 @@ CACHE_PATH = os.environ.get("HX_TUNE_CACHE",
 _lock = threading.Lock()
 
 
-#: per-pass kernel variants: (logR, pipe, np) -- 16 or 8 elements per thread,
-#: plain or persistent, one or two polynomials per thread
-VARIANTS = ((3, 0, 1), (4, 0, 1), (3, 1, 1), (4, 1, 1), (3, 0, 2))
+#: per-pass kernel variants: (logR, pipe, np) -- 16 or 8 elements per thread;
+#: per-tile kernel with twiddles read through the read-only cache (pipe 0),
+#: persistent double-buffered kernel (1), per-tile kernel with the tile's
+#: twiddles staged in shared memory (2); one or two polynomials per thread
+VARIANTS = ((3, 0, 1), (4, 0, 1), (3, 1, 1), (4, 1, 1), (3, 0, 2), (3, 2, 1), (4, 2, 1),
+            (3, 2, 2))
+
+
+def single_pass(logN: int, variants=VARIANTS) -> List[List[Pass]]:
+    return [[(0, logN, 0, 0) + v] for v in variants] if logN <= 13 else []
+
+
+def splits(logN: int) -> List[int]:
+    """First-pass stage counts K1 of the two-pass schedules (both passes 6..13 stages)."""
+    return [K1 for K1 in range(6, 10) if 6 <= logN - K1 <= 13]
+
+
+def pass_options(logN: int, K1: int, variants=VARIANTS) -> Tuple[List[Pass], List[Pass]]:
+    """(first-pass options, second-pass options) of the split at K1: column
+    passes over stages [0, K1) in 2^logGc-column tiles, row passes over the
+    rest in 2^logGb-row tiles, each with every kernel variant."""
+    firsts = [(0, K1, 0, logGc) + v for logGc in (2, 3, 4, 5) for v in variants]
+    seconds = [(K1, logN - K1, logGb, 0) + v for logGb in range(0, 6) for v in variants]
+    return firsts, seconds
 
 
 def candidates(logN: int, variants=VARIANTS) -> List[List[Pass]]:
-    """Schedules worth trying for log2 N (validity is checked by the library)."""
-    out: List[List[Pass]] = []
-    if logN <= 13:
-        for logR, pipe, np_ in variants:
-            out.append([(0, logN, 0, 0, logR, pipe, np_)])
-    for K1 in range(6, 10):
-        K2 = logN - K1
-        if not 6 <= K2 <= 13:
-            continue
-        for logGc in (2, 3, 4, 5):
-            for v1 in variants:
-                for logGb in range(0, 6):
-                    for v2 in variants:
-                        out.append([(0, K1, 0, logGc) + v1, (K1, K2, logGb, 0) + v2])
+    """Every schedule worth trying for log2 N (validity is checked by the library)."""
+    out = single_pass(logN, variants)
+    for K1 in splits(logN):
+        firsts, seconds = pass_options(logN, K1, variants)
+        out += [[a, b] for a in firsts for b in seconds]
     return out
 
 
@@ -82,23 +99,94 @@ def save_cache(cache: Dict[str, dict]) -> None:
     os.replace(tmp, CACHE_PATH)
 
 
-def time_schedule(plan, sched, x, y, n_polys: int, iters: int = 5) -> Tuple[float, float]:
-    """(forward us, inverse us) per call for one schedule, averaged over iters."""
+def _valid_pair(plan, firsts: List[Pass], seconds: List[Pass]):
+    """One valid (first pass, second pass) pair, or None.  Validity is a
+    property of each pass on its own, so a pass that is valid with one
+    partner is valid with every valid partner."""
+    for b in seconds:
+        for a in firsts:
+            if valid(plan, [a, b]):
+                return a, b
+    return None
+
+
+def covering(plan: "capi.Plan", variants=VARIANTS) -> List[List[Pass]]:
+    """Valid schedules that between them use every valid pass configuration:
+    the single-pass ones, and per split each valid first pass with one valid
+    second pass and each valid second pass with one valid first pass."""
+    logN = plan.N.bit_length() - 1
+    out = [s for s in single_pass(logN, variants) if valid(plan, s)]
+    for K1 in splits(logN):
+        firsts, seconds = pass_options(logN, K1, variants)
+        pair = _valid_pair(plan, firsts, seconds)
+        if pair is None:
+            continue
+        a0, b0 = pair
+        out += [[a, b0] for a in firsts if valid(plan, [a, b0])]
+        out += [[a0, b] for b in seconds if b != b0 and valid(plan, [a0, b])]
+    return out
+
+
+def time_schedule(plan, sched, x, y, n_polys: int, iters: int = 5,
+                  direction: int = 3) -> Tuple[float, float]:
+    """(forward us, inverse us) per call for one schedule, averaged over
+    iters; a direction not asked for is reported as inf."""
     import torch
     plan.set_schedule(sched, plan.BOTH)
     st = torch.cuda.current_stream()
-    capi.hx_ntt_forward(plan, y, x, n_polys, 1, 4, st)
-    capi.hx_ntt_inverse(plan, y, y, n_polys, 1, 1, st)
+    if direction & 1:
+        capi.hx_ntt_forward(plan, y, x, n_polys, 1, 4, st)
+    if direction & 2:
+        capi.hx_ntt_inverse(plan, y, x, n_polys, 1, 1, st)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     ev[0].record(st)
-    for _ in range(iters):
+    for _ in range(iters if direction & 1 else 0):
         capi.hx_ntt_forward(plan, y, x, n_polys, 1, 4, st)
     ev[1].record(st)
-    for _ in range(iters):
-        capi.hx_ntt_inverse(plan, y, y, n_polys, 1, 1, st)
+    for _ in range(iters if direction & 2 else 0):
+        capi.hx_ntt_inverse(plan, y, x, n_polys, 1, 1, st)
     ev[2].record(st)
     torch.cuda.synchronize()
-    return ev[0].elapsed_time(ev[1]) * 1e3 / iters, ev[1].elapsed_time(ev[2]) * 1e3 / iters
+    f = ev[0].elapsed_time(ev[1]) * 1e3 / iters if direction & 1 else float("inf")
+    i = ev[1].elapsed_time(ev[2]) * 1e3 / iters if direction & 2 else float("inf")
+    return f, i
+
+
+def _search(plan, x, y, n_polys: int, iters: int, d: int, verbose: bool):
+    """Fastest schedule for one direction (d = 1 forward, 2 inverse): every
+    single-pass schedule, and per split a coordinate search -- the best first
+    pass against a fixed valid second pass, then the best second pass
+    against that first pass.  The passes are separate launches, so a
+    schedule's time is the sum of its passes' and the search finds the best
+    pair.  Returns (us, schedule, schedules timed)."""
+    logN = plan.N.bit_length() - 1
+    k = 0 if d == 1 else 1
+    best, tried = (float("inf"), None), 0
+
+    def run(s):
+        nonlocal best, tried
+        t = time_schedule(plan, s, x, y, n_polys, iters, d)[k]
+        tried += 1
+        if verbose:
+            print(f"{'fwd' if d == 1 else 'inv'} {t:9.1f}  {s}", file=sys.stderr)
+        if t < best[0]:
+            best = (t, s)
+        return t
+
+    for s in single_pass(logN):
+        if valid(plan, s):
+            run(s)
+    for K1 in splits(logN):
+        firsts, seconds = pass_options(logN, K1)
+        pair = _valid_pair(plan, firsts, seconds)
+        if pair is None:
+            continue
+        b0 = pair[1]
+        a_best = min((a for a in firsts if valid(plan, [a, b0])), key=lambda a: run([a, b0]))
+        for b in seconds:
+            if b != b0 and valid(plan, [a_best, b]):
+                run([a_best, b])
+    return best[0], best[1], tried
 
 
 def tune(plan: "capi.Plan", n_polys: int, scheds: Optional[Iterable[List[Pass]]] = None,
@@ -107,8 +195,9 @@ def tune(plan: "capi.Plan", n_polys: int, scheds: Optional[Iterable[List[Pass]]]
     """Pick the fastest forward and the fastest inverse schedule for this plan
     and batch size, apply them to the plan (only the forward one for
     direction 1, only the inverse one for 2) and return {"forward",
-    "inverse", "fwd_us", "inv_us", "tried"}.  Inputs are uniform synthetic
-    residues."""
+    "inverse", "fwd_us", "inv_us", "tried"}.  Without `scheds` the search of
+    _search runs; with it, exactly those schedules are timed.  Inputs are
+    uniform synthetic residues."""
     import torch
     from .tensors import to_device, empty
     import numpy as np
@@ -135,22 +224,29 @@ def tune(plan: "capi.Plan", n_polys: int, scheds: Optional[Iterable[List[Pass]]]
     for l, q in enumerate(plan.moduli):
         host[:, l] = rng.integers(0, q, size=(n_polys, plan.N), dtype=np.uint64)
     x, y = to_device(host), empty(host.shape)
-    logN = plan.N.bit_length() - 1
-    results = []
-    for sched in (scheds if scheds is not None else candidates(logN)):
-        if not valid(plan, sched):
-            continue
-        f, i = time_schedule(plan, sched, x, y, n_polys, iters)
-        results.append((f, i, sched))
-        if verbose:
-            print(f"{f:9.1f} {i:9.1f}  {sched}")
-    if not results:
+    if scheds is None:
+        fu, fs, nf = _search(plan, x, y, n_polys, iters, 1, verbose)
+        iu, is_, ni = _search(plan, x, y, n_polys, iters, 2, verbose)
+        tried = nf + ni
+    else:
+        results = []
+        for sched in scheds:
+            if not valid(plan, sched):
+                continue
+            f, i = time_schedule(plan, sched, x, y, n_polys, iters)
+            results.append((f, i, sched))
+            if verbose:
+                print(f"{f:9.1f} {i:9.1f}  {sched}", file=sys.stderr)
+        if not results:
+            raise RuntimeError("no valid schedule")
+        fu, fs = min((r[0], r[2]) for r in results)
+        iu, is_ = min((r[1], r[2]) for r in results)
+        tried = len(results)
+    if fs is None or is_ is None:
         raise RuntimeError("no valid schedule")
-    bf = min(results, key=lambda r: r[0])
-    bi = min(results, key=lambda r: r[1])
-    apply(bf[2], bi[2])
-    out = {"forward": [list(p) for p in bf[2]], "inverse": [list(p) for p in bi[2]],
-           "fwd_us": bf[0], "inv_us": bi[1], "tried": len(results)}
+    apply(fs, is_)
+    out = {"forward": [list(p) for p in fs], "inverse": [list(p) for p in is_],
+           "fwd_us": fu, "inv_us": iu, "tried": tried}
     if use_cache:
         with _lock:
             cache = load_cache()
