@@ -106,7 +106,7 @@ class HexStep:
         self.plan = capi.Plan(N, moduli)
         if tune:
             self.tuned = {"forward": hx_tune.tune(self.plan, 4, direction=capi.Plan.FORWARD),
-                          "inverse": hx_tune.tune(self.plan, 3, direction=capi.Plan.INVERSE)}
+                          "inverse": hx_tune.tune_tensor(self.plan, 1, s)}
         self.dev_sets = dev_sets
         L = len(moduli)
         self.A = empty((4, L, N))
@@ -126,9 +126,10 @@ class HexStep:
             e1.record(st)
             self.fwd_events.append((e0, e1))
         A, R = self.A, self.R
-        c.hx_dyadic_tensor_fma(R[0], R[1], R[2], A[0], A[1], A[2], A[3], self.s, es[0], es[1],
-                               es[2], N, self.moduli, 1, 4, st)
-        c.hx_ntt_inverse(self.plan, R, R, 3, 1, 1, st)
+        # tensor, FMA and inverse NTT: the element-wise step runs inside the
+        # inverse's first pass (operands back to back)
+        c.hx_tensor_fma_inverse(self.plan, R[0], R[1], R[2], A[0], A[1], A[2], A[3], self.s,
+                                es[0], es[1], es[2], 1, 4, st)
         return [R[0:1], R[1:2], R[2:3]]
 
 
@@ -443,6 +444,8 @@ def run_case(args):
         return 0
     wl = W.ciphertext_tensor(N=N, n_limbs=nl)
     P = args.polys
+    if args.case == "tensor_inv":
+        return run_tensor_inv(args, wl, torch)
     n_sets = 2
     xs = [to_device(W.poly_batch(wl.seed + k, 0, P, wl.moduli, N)) for k in range(n_sets)]
     ys = [empty(x.shape) for x in xs]
@@ -489,6 +492,47 @@ def run_case(args):
     return 0
 
 
+def run_tensor_inv(args, wl, torch):
+    """hx_tensor_fma_inverse on one ciphertext pair: its tuned schedule, the
+    fused call's time, and the composed path (element-wise kernel, then the
+    inverse transform) on the same schedule (diagnostic line)."""
+    from paper_2103_16400_gb300 import capi, tune as hx_tune
+    from paper_2103_16400_gb300.tensors import empty, to_device
+    N, nl = args.N, args.limbs
+    plan = capi.Plan(N, wl.moduli)
+    s = W.scalars(wl.seed, 20, wl.moduli)
+    t = hx_tune.tune_tensor(plan, 1, s, verbose=bool(os.environ.get("HX_TUNE_VERBOSE")))
+    A = to_device(np.stack([W.poly_batch(wl.seed, k, 1, wl.moduli, N) for k in range(4)]))
+    E = to_device(np.stack([W.poly_batch(wl.seed, 10 + k, 1, wl.moduli, N) for k in range(3)]))
+    R = empty((3, 1, nl, N))
+    st = torch.cuda.current_stream()
+
+    def fused():
+        capi.hx_tensor_fma_inverse(plan, R[0], R[1], R[2], A[0], A[1], A[2], A[3], s, E[0],
+                                   E[1], E[2], 1, 4, st)
+
+    def composed():
+        capi.hx_dyadic_tensor_fma(R[0], R[1], R[2], A[0], A[1], A[2], A[3], s, E[0], E[1], E[2],
+                                  N, wl.moduli, 1, 4, st)
+        capi.hx_ntt_inverse(plan, R, R, 3, 1, 1, st)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / args.steps
+
+    print(json.dumps({"case": "tensor_inv", "N": N, "limbs": nl, "schedule": t["inverse"],
+                      "fused_us": timed(fused), "composed_us": timed(composed)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -505,7 +549,7 @@ def main():
                     help="skip the serving report (Poisson arrivals, p50/p99 latency)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--case", default="pipeline",
-                    choices=["pipeline", "fwd", "inv", "tensor", "probes"],
+                    choices=["pipeline", "fwd", "inv", "tensor", "tensor_inv", "probes"],
                     help="pipeline: the contract line; others: one kernel family alone "
                          "(diagnostic line, used for profiling)")
     ap.add_argument("--polys", type=int, default=8, help="polynomials per call for --case fwd/inv")

@@ -209,10 +209,26 @@ int hx_eltwise_fma_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* 
  *     d0 = A0 B0,  d1 = A0 B1 + A1 B0,  d2 = A1 B1   (element-wise mod q)
  *     r_k = d_k * s_l + e_k mod q                    (EltwiseFMAMod)
  *     out_k = inverse NTT of r_k, in [0, q).
- *   The products, the sum and the scaling run in one fused element-wise
- *   kernel; all steps are enqueued on `stream`.  e_k are in [0, q) (NTT
- *   domain); h_scalars holds one s_l in [0, q) per limb.  The four inputs
- *   are overwritten with their transforms; out_k must not alias any input.
+ *   The products, the sum, the scaling and the inverse transform run as
+ *   hx_tensor_fma_inverse below; all steps are enqueued on `stream`.  e_k
+ *   are in [0, q) (NTT domain); h_scalars holds one s_l in [0, q) per limb.
+ *   The four inputs are overwritten with their transforms; out_k must not
+ *   alias any input.
+ *
+ * hx_tensor_fma_inverse: the NTT-domain half of hx_ciphertext_tensor --
+ *   from forward transforms A0, A1, B0, B1 in [0, input_mod_factor q)
+ *   (input_mod_factor in {1, 2, 4}) and addends e_k in [0, q):
+ *     r_k = d_k s_l + e_k mod q (d_k as above),  out_k = inverse NTT of r_k,
+ *   in [0, q).  When A0..B1 lie back to back from A0 ([4][n_polys][limbs][N]),
+ *   e0..e2 from e0 and out0..out2 from out0 ([3][n_polys][limbs][N]), and
+ *   the plan's inverse schedule starts with a per-tile pass (pipe 0 or 2),
+ *   the element-wise step runs inside the first pass of the inverse
+ *   transform, so the r_k are never written to device memory (cross-kernel
+ *   fusion, the direction Section 5 names); otherwise it runs as
+ *   hx_dyadic_tensor_fma followed by hx_ntt_inverse.  Both give the same
+ *   bits.  Moduli must be < 2^61; out_k must not alias any input.  Errors:
+ *   HX_ERR_NULL, HX_ERR_ARG, HX_ERR_MOD_FACTOR, HX_ERR_MODULUS, HX_ERR_ALIGN,
+ *   HX_ERR_OVERLAP, HX_ERR_CUDA.
  */
 int hx_poly_mul(hx_plan_t plan, uint64_t* d_result, uint64_t* d_a, uint64_t* d_b,
                 uint32_t n_polys, hx_stream_t stream);
@@ -220,6 +236,12 @@ int hx_ciphertext_tensor(hx_plan_t plan, uint64_t* d_out0, uint64_t* d_out1, uin
                          uint64_t* d_a0, uint64_t* d_a1, uint64_t* d_b0, uint64_t* d_b1,
                          const uint64_t* h_scalars, const uint64_t* d_e0, const uint64_t* d_e1,
                          const uint64_t* d_e2, uint32_t n_polys, hx_stream_t stream);
+
+int hx_tensor_fma_inverse(hx_plan_t plan, uint64_t* d_out0, uint64_t* d_out1, uint64_t* d_out2,
+                          const uint64_t* d_A0, const uint64_t* d_A1, const uint64_t* d_B0,
+                          const uint64_t* d_B1, const uint64_t* h_scalars, const uint64_t* d_e0,
+                          const uint64_t* d_e1, const uint64_t* d_e2, uint32_t n_polys,
+                          uint32_t input_mod_factor, hx_stream_t stream);
 
 /* Fused element-wise part of hx_ciphertext_tensor on its own: reads A0, A1,
  * B0, B1 in [0, input_mod_factor q) (input_mod_factor in {1, 2, 4}) and e_k

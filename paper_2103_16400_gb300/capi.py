@@ -40,6 +40,7 @@ _SIGS = {
     "hx_eltwise_fma_mod": [VP, VP, P64, VP, U64, P64, U32, U32, U32, VP],
     "hx_poly_mul": [VP, VP, VP, VP, U32, VP],
     "hx_ciphertext_tensor": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, VP],
+    "hx_tensor_fma_inverse": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, U32, VP],
     "hx_dyadic_tensor_fma": [VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U64, P64, U32, U32,
                              U32, VP],
     "hx_batch_create": [ctypes.POINTER(VP), VP, U32, U32, U32, U32],
@@ -322,6 +323,14 @@ def hx_ciphertext_tensor(plan, out0, out1, out2, a0, a1, b0, b1, scalars, e0, e1
     _check("hx_ciphertext_tensor", load().hx_ciphertext_tensor(
         _h(plan), ptr(out0), ptr(out1), ptr(out2), ptr(a0), ptr(a1), ptr(b0), ptr(b1),
         host_u64(scalars), ptr(e0), ptr(e1), ptr(e2), n_polys, _stream(stream)))
+
+
+def hx_tensor_fma_inverse(plan, out0, out1, out2, A0, A1, B0, B1, scalars, e0, e1, e2,
+                          n_polys: int, input_mod_factor: int = 4, stream=None):
+    _check("hx_tensor_fma_inverse", load().hx_tensor_fma_inverse(
+        _h(plan), ptr(out0), ptr(out1), ptr(out2), ptr(A0), ptr(A1), ptr(B0), ptr(B1),
+        host_u64(scalars), ptr(e0), ptr(e1), ptr(e2), n_polys, input_mod_factor,
+        _stream(stream)))
 
 
 def hx_dyadic_tensor_fma(r0, r1, r2, A0, A1, B0, B1, scalars, e0, e1, e2, n: int, moduli,

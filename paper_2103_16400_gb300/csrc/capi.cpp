@@ -252,6 +252,46 @@ int hx_poly_mul(hx_plan_t plan, uint64_t* r, uint64_t* a, uint64_t* b, uint32_t 
     return hx_ntt_inverse(plan, r, r, n_polys, 1, 1, stream);
 }
 
+int hx_tensor_fma_inverse(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* o2,
+                          const uint64_t* A0, const uint64_t* A1, const uint64_t* B0,
+                          const uint64_t* B1, const uint64_t* h_scalars, const uint64_t* e0,
+                          const uint64_t* e1, const uint64_t* e2, uint32_t n_polys,
+                          uint32_t in_mf, hx_stream_t stream) {
+    if (!plan || !o0 || !o1 || !o2 || !A0 || !A1 || !B0 || !B1 || !h_scalars || !e0 || !e1 ||
+        !e2)
+        return HX_ERR_NULL;
+    if (n_polys == 0 || (uint64_t)n_polys * 4 * plan->n_limbs > (1ull << 31)) return HX_ERR_ARG;
+    const uint64_t S = (uint64_t)n_polys * plan->n_limbs * plan->N;
+    const bool fused_layout = A1 == A0 + S && B0 == A0 + 2 * S && B1 == A0 + 3 * S &&
+                              e1 == e0 + S && e2 == e0 + 2 * S && o1 == o0 + S && o2 == o0 + 2 * S;
+    if (fused_layout && tensor_fusable(plan->cfg_inv)) {
+        // the element-wise step's checks: moduli < 2^61, scalars < q,
+        // alignment, outputs disjoint from every input
+        if (!(in_mf == 1 || in_mf == 2 || in_mf == 4)) return HX_ERR_MOD_FACTOR;
+        for (uint32_t l = 0; l < plan->n_limbs; ++l) {
+            const uint64_t q = plan->moduli[l];
+            if (q >= (1ull << 61)) return HX_ERR_MODULUS;
+            if (h_scalars[l] >= q) return HX_ERR_ARG;
+        }
+        if (!aligned16(o0) || !aligned16(A0) || !aligned16(e0)) return HX_ERR_ALIGN;
+        const uintptr_t x = (uintptr_t)o0, xe = x + 3 * S * 8;
+        const uintptr_t a = (uintptr_t)A0, ae = a + 4 * S * 8;
+        const uintptr_t e = (uintptr_t)e0, ee = e + 3 * S * 8;
+        if ((x < ae && a < xe) || (x < ee && e < xe)) return HX_ERR_OVERLAP;
+        return cuda_status(launch_tensor_inverse(plan, o0, A0, e0, n_polys, h_scalars, in_mf,
+                                                 plan->cfg_inv, (cudaStream_t)stream));
+    }
+    int st = hx_dyadic_tensor_fma(o0, o1, o2, A0, A1, B0, B1, h_scalars, e0, e1, e2, plan->N,
+                                  plan->moduli.data(), plan->n_limbs, n_polys, in_mf, stream);
+    if (st != HX_OK) return st;
+    if (o1 == o0 + S && o2 == o0 + 2 * S)
+        return hx_ntt_inverse(plan, o0, o0, 3 * n_polys, 1, 1, stream);
+    uint64_t* outs[3] = {o0, o1, o2};
+    for (auto y : outs)
+        if ((st = hx_ntt_inverse(plan, y, y, n_polys, 1, 1, stream)) != HX_OK) return st;
+    return HX_OK;
+}
+
 int hx_ciphertext_tensor(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* o2, uint64_t* a0,
                          uint64_t* a1, uint64_t* b0, uint64_t* b1, const uint64_t* h_scalars,
                          const uint64_t* e0, const uint64_t* e1, const uint64_t* e2,
@@ -270,17 +310,8 @@ int hx_ciphertext_tensor(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* o
         for (auto x : ins)
             if ((st = hx_ntt_forward(plan, x, x, n_polys, 1, 4, stream)) != HX_OK) return st;
     }
-    st = hx_dyadic_tensor_fma(o0, o1, o2, a0, a1, b0, b1, h_scalars, e0, e1, e2, plan->N,
-                              plan->moduli.data(), plan->n_limbs, n_polys, 4, stream);
-    if (st != HX_OK) return st;
-    uint64_t* outs[3] = {o0, o1, o2};
-    if (o1 == o0 + S && o2 == o0 + 2 * S) {
-        if ((st = hx_ntt_inverse(plan, o0, o0, 3 * n_polys, 1, 1, stream)) != HX_OK) return st;
-    } else {
-        for (auto x : outs)
-            if ((st = hx_ntt_inverse(plan, x, x, n_polys, 1, 1, stream)) != HX_OK) return st;
-    }
-    return HX_OK;
+    return hx_tensor_fma_inverse(plan, o0, o1, o2, a0, a1, b0, b1, h_scalars, e0, e1, e2, n_polys,
+                                 4, stream);
 }
 
 }  // extern "C"

@@ -48,11 +48,6 @@ __device__ __forceinline__ uint64_t row_offset(const EltGeom& g, uint32_t row, u
     return ((uint64_t)poly * g.n_limbs + g.limb0 + li) * g.n;
 }
 
-__device__ __forceinline__ uint64_t fma_shoup(uint64_t a, uint64_t s, uint64_t sp, uint64_t q) {
-    uint64_t r = s * a - mulhi64(sp, a) * q;  // [0, 2q)
-    return r >= q ? r - q : r;
-}
-
 template <int OP, int INMF, bool ADDEND>
 __device__ __forceinline__ uint64_t elt_apply(uint64_t a, uint64_t b, const EltConsts& c,
                                               uint32_t li) {
@@ -122,20 +117,9 @@ __global__ void __launch_bounds__(256) tensor_fma_kernel(
         const uint64_t j = off + i;
         const uint64_t a0 = small_mod<INMF>(A0[j], q), a1 = small_mod<INMF>(A1[j], q);
         const uint64_t b0 = small_mod<INMF>(B0[j], q), b1 = small_mod<INMF>(B1[j], q);
-        // d1 = a0 b1 + a1 b0 as one 128-bit sum (< 2 q^2 < 2^(2Q+1)), one Barrett
-        uint64_t lo = a0 * b1, hi = mulhi64(a0, b1);
-        const uint64_t lo2 = a1 * b0, hi2 = mulhi64(a1, b0);
-        lo += lo2;
-        hi += hi2 + (lo < lo2 ? 1 : 0);
-        const uint64_t d0 = barrett_mulmod(a0, b0, br);
-        const uint64_t d1 = barrett_reduce128(hi, lo, br);
-        const uint64_t d2 = barrett_mulmod(a1, b1, br);
-        uint64_t t0 = fma_shoup(d0, s, sp, q) + e0[j];
-        uint64_t t1 = fma_shoup(d1, s, sp, q) + e1[j];
-        uint64_t t2 = fma_shoup(d2, s, sp, q) + e2[j];
-        r0[j] = t0 >= q ? t0 - q : t0;
-        r1[j] = t1 >= q ? t1 - q : t1;
-        r2[j] = t2 >= q ? t2 - q : t2;
+        r0[j] = tensor_r(tensor_d(0, a0, a1, b0, b1, br), e0[j], s, sp, q);
+        r1[j] = tensor_r(tensor_d(1, a0, a1, b0, b1, br), e1[j], s, sp, q);
+        r2[j] = tensor_r(tensor_d(2, a0, a1, b0, b1, br), e2[j], s, sp, q);
     }
 }
 

@@ -85,6 +85,14 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
                        uint32_t n_polys, bool forward, uint32_t in_mf, uint32_t out_mf,
                        const NttCfg& cfg, cudaStream_t stream);
 bool cfg_supported(int logN, const NttCfg& cfg);
+// Inverse transform of the three ciphertext-tensor terms with the element-
+// wise step in its first pass: out = [3][n_ct][limbs][N] from A = [4][n_ct]..
+// (forward outputs, < in_mf q) and E = [3][n_ct].. (< q).  cudaErrorNotSupported
+// when the schedule's first inverse pass is not a per-tile row pass.
+bool tensor_fusable(const NttCfg& cfg);
+cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const uint64_t* A,
+                                  const uint64_t* E, uint32_t n_ct, const uint64_t* h_scalars,
+                                  uint32_t in_mf, const NttCfg& cfg, cudaStream_t stream);
 
 // eltwise.cu
 enum EltOp { ELT_ADD = 0, ELT_SUB = 1, ELT_MULT = 2, ELT_FMA = 3 };

@@ -223,4 +223,33 @@ __device__ __forceinline__ uint64_t barrett_mulmod(uint64_t x, uint64_t y, const
     return barrett_reduce128(mulhi64(x, y), x * y, b);
 }
 
+// a s mod q in [0, q) for a < 2^64, s < q, sp = floor(s 2^64 / q): the Shoup
+// product of Algorithm "EltwiseFMAModAVX512" ([0, 2q)) and one subtraction.
+__device__ __forceinline__ uint64_t fma_shoup(uint64_t a, uint64_t s, uint64_t sp, uint64_t q) {
+    uint64_t r = s * a - mulhi64(sp, a) * q;  // [0, 2q)
+    return r >= q ? r - q : r;
+}
+
+// ---------------------------------------------------------------- ciphertext tensor
+// Term k of the element-wise ciphertext tensor from residues in [0, q):
+// d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1 (mod q).  d1 reduces the
+// 128-bit sum of the two products (< 2 q^2 < 2^(2Q+1)) with one Barrett.
+__device__ __forceinline__ uint64_t tensor_d(uint32_t k, uint64_t a0, uint64_t a1, uint64_t b0,
+                                             uint64_t b1, const Barrett& br) {
+    if (k == 0) return barrett_mulmod(a0, b0, br);
+    if (k == 2) return barrett_mulmod(a1, b1, br);
+    uint64_t lo = a0 * b1, hi = mulhi64(a0, b1);
+    const uint64_t lo2 = a1 * b0, hi2 = mulhi64(a1, b0);
+    lo += lo2;
+    hi += hi2 + (lo < lo2 ? 1 : 0);
+    return barrett_reduce128(hi, lo, br);
+}
+
+// r = d s + e mod q in [0, q) (EltwiseFMAMod with addend), d, e in [0, q).
+__device__ __forceinline__ uint64_t tensor_r(uint64_t d, uint64_t e, uint64_t s, uint64_t sp,
+                                             uint64_t q) {
+    const uint64_t t = fma_shoup(d, s, sp, q) + e;
+    return t >= q ? t - q : t;
+}
+
 }  // namespace hx

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "ntt_kernels.cuh"
+#include "ntt_tensor.h"
 
 namespace hx {
 
@@ -92,53 +93,119 @@ static int resident_blocks(PassKernel k, int threads, size_t smem, int* sms) {
     return it->second.first;
 }
 
+// Launches one pass of a schedule over n_polys polynomials.
+static cudaError_t launch_pass(const hx_plan_s* plan, const PassCfg& p, uint64_t* out,
+                               const uint64_t* in, uint32_t n_polys, bool forward, bool last,
+                               uint32_t out_mf, cudaStream_t stream) {
+    const int L = plan->logN;
+    PassArgs a;
+    a.out = out;
+    a.in = in;
+    a.limbs = plan->d_limbs;
+    a.n_limbs = plan->n_limbs;
+    a.n_polys = n_polys;
+    a.L = L;
+    a.s0 = p.s0;
+    a.logGb = p.logGb;
+    a.logGc = p.logGc;
+    a.log_tiles_c = (L - p.s0 - p.K) - p.logGc;
+    a.last = last;
+    a.out_mf = out_mf;
+    const int logTE = p.logGb + p.K + p.logGc;
+    const uint32_t tiles = 1u << (L - logTE);
+    const uint32_t threads = 1u << (logTE - p.logR);
+    const size_t smem = pass_smem(p);
+    PassKernel k = pick(forward, p);
+    if (!k) return cudaErrorInvalidConfiguration;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)k,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (p.pipe == 1) {
+        int sms = 0;
+        const int per_sm = resident_blocks(k, threads, smem, &sms);
+        const uint64_t total = (uint64_t)tiles * n_polys * plan->n_limbs;
+        const uint64_t grid = std::min<uint64_t>(total, (uint64_t)per_sm * sms);
+        k<<<(unsigned)grid, threads, smem, stream>>>(a);
+    } else {
+        dim3 grid(tiles * ((n_polys + p.np - 1) / p.np), plan->n_limbs);
+        k<<<grid, threads, smem, stream>>>(a);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
                        uint32_t n_polys, bool forward, uint32_t in_mf, uint32_t out_mf,
                        const NttCfg& cfg, cudaStream_t stream) {
     (void)in_mf;  // every allowed input range is inside the butterflies' lazy range
-    const int L = plan->logN;
     for (int step = 0; step < cfg.npass; ++step) {
         const int pi = forward ? step : cfg.npass - 1 - step;
-        const PassCfg& p = cfg.pass[pi];
-        PassArgs a;
-        a.out = out;
-        a.in = step == 0 ? in : out;
-        a.limbs = plan->d_limbs;
-        a.n_limbs = plan->n_limbs;
-        a.n_polys = n_polys;
-        a.L = L;
-        a.s0 = p.s0;
-        a.logGb = p.logGb;
-        a.logGc = p.logGc;
-        a.log_tiles_c = (L - p.s0 - p.K) - p.logGc;
-        a.last = step == cfg.npass - 1;
-        a.out_mf = out_mf;
-        const int logTE = p.logGb + p.K + p.logGc;
-        const uint32_t tiles = 1u << (L - logTE);
-        const uint32_t threads = 1u << (logTE - p.logR);
-        const size_t smem = pass_smem(p);
-        PassKernel k = pick(forward, p);
-        if (!k) return cudaErrorInvalidConfiguration;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute((const void*)k,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
+        cudaError_t e = launch_pass(plan, cfg.pass[pi], out, step == 0 ? in : out, n_polys,
+                                    forward, step == cfg.npass - 1, out_mf, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+bool tensor_fusable(const NttCfg& cfg) {
+    const PassCfg& p = cfg.pass[cfg.npass - 1];   // the inverse runs this pass first
+    return p.pipe != 1 && p.logGc == 0 && pick_tensor_inv(p.logR, p.K, p.pipe == 2) != nullptr;
+}
+
+cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const uint64_t* A,
+                                  const uint64_t* E, uint32_t n_ct, const uint64_t* h_scalars,
+                                  uint32_t in_mf, const NttCfg& cfg, cudaStream_t stream) {
+    if (!tensor_fusable(cfg)) return cudaErrorNotSupported;
+    const int L = plan->logN;
+    const PassCfg& p = cfg.pass[cfg.npass - 1];
+    TensorPassKernel k = pick_tensor_inv(p.logR, p.K, p.pipe == 2);
+    PassArgs a;
+    a.out = out;
+    a.in = nullptr;
+    a.limbs = plan->d_limbs;
+    a.n_limbs = plan->n_limbs;
+    a.n_polys = 3 * n_ct;
+    a.L = L;
+    a.s0 = p.s0;
+    a.logGb = p.logGb;
+    a.logGc = 0;
+    a.log_tiles_c = 0;
+    a.last = cfg.npass == 1;
+    a.out_mf = 1;
+    const int logTE = p.logGb + p.K;
+    const uint32_t tiles = 1u << (L - logTE);
+    const uint32_t threads = 1u << (logTE - p.logR);
+    const size_t smem = (size_t)8 * padded(1u << logTE) +
+                        (p.pipe == 2 ? 16 * (size_t)staged_twiddles(p.logGb, p.K) : 0);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)k,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    for (uint32_t limb0 = 0; limb0 < plan->n_limbs; limb0 += kTensorLimbs) {
+        const uint32_t chunk = std::min<uint32_t>(kTensorLimbs, plan->n_limbs - limb0);
+        TensorIn t{};
+        t.A = A;
+        t.E = E;
+        t.n_ct = n_ct;
+        t.in_mf = in_mf;
+        t.limb0 = limb0;
+        for (uint32_t i = 0; i < chunk; ++i) {
+            const uint64_t q = plan->moduli[limb0 + i], sc = h_scalars[limb0 + i];
+            t.s[i] = sc;
+            t.sp[i] = (uint64_t)(((unsigned __int128)sc << 64) / q);
         }
-        if (p.pipe == 1) {
-            int sms = 0;
-            const int per_sm = resident_blocks(k, threads, smem, &sms);
-            const uint64_t total = (uint64_t)tiles * n_polys * plan->n_limbs;
-            const uint64_t grid = std::min<uint64_t>(total, (uint64_t)per_sm * sms);
-            k<<<(unsigned)grid, threads, smem, stream>>>(a);
-        } else {
-            dim3 grid(tiles * ((n_polys + p.np - 1) / p.np), plan->n_limbs);
-            k<<<grid, threads, smem, stream>>>(a);
-        }
+        k<<<dim3(tiles * 3 * n_ct, chunk), threads, smem, stream>>>(a, t);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (cfg.npass == 2)
+        return launch_pass(plan, cfg.pass[0], out, out, 3 * n_ct, false, true, 1, stream);
     return cudaSuccess;
 }
 

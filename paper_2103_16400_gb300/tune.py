@@ -67,11 +67,17 @@ def candidates(logN: int, variants=VARIANTS) -> List[List[Pass]]:
 
 
 def valid(plan: "capi.Plan", sched: List[Pass]) -> bool:
+    """Whether the library can run `sched` on this plan; the plan's own
+    schedules are left as they were."""
+    keep = (plan.schedule(plan.FORWARD), plan.schedule(plan.INVERSE))
     try:
         plan.set_schedule(sched)
         return True
     except capi.HexError:
         return False
+    finally:
+        plan.set_schedule(keep[0], plan.FORWARD)
+        plan.set_schedule(keep[1], plan.INVERSE)
 
 
 def width_class(moduli: Sequence[int]) -> str:
@@ -152,23 +158,22 @@ def time_schedule(plan, sched, x, y, n_polys: int, iters: int = 5,
     return f, i
 
 
-def _search(plan, x, y, n_polys: int, iters: int, d: int, verbose: bool):
-    """Fastest schedule for one direction (d = 1 forward, 2 inverse): every
-    single-pass schedule, and per split a coordinate search -- the best first
-    pass against a fixed valid second pass, then the best second pass
-    against that first pass.  The passes are separate launches, so a
-    schedule's time is the sum of its passes' and the search finds the best
-    pair.  Returns (us, schedule, schedules timed)."""
+def _search(plan, timer, label: str, verbose: bool):
+    """Fastest schedule by `timer(schedule) -> us`: every single-pass
+    schedule, and per split a coordinate search -- the best first pass
+    against a fixed valid second pass, then the best second pass against that
+    first pass.  The passes are separate launches, so a schedule's time is the
+    sum of its passes' and the search finds the best pair.  Returns (us,
+    schedule, schedules timed)."""
     logN = plan.N.bit_length() - 1
-    k = 0 if d == 1 else 1
     best, tried = (float("inf"), None), 0
 
     def run(s):
         nonlocal best, tried
-        t = time_schedule(plan, s, x, y, n_polys, iters, d)[k]
+        t = timer(s)
         tried += 1
         if verbose:
-            print(f"{'fwd' if d == 1 else 'inv'} {t:9.1f}  {s}", file=sys.stderr)
+            print(f"{label} {t:9.1f}  {s}", file=sys.stderr)
         if t < best[0]:
             best = (t, s)
         return t
@@ -203,7 +208,7 @@ def tune(plan: "capi.Plan", n_polys: int, scheds: Optional[Iterable[List[Pass]]]
     import numpy as np
 
     name = torch.cuda.get_device_name()
-    key = _key(plan.N, plan.moduli, n_polys, name)
+    key = _key(plan.N, plan.moduli, n_polys, name) + f"|d={direction}"
     keep = (plan.schedule(plan.FORWARD), plan.schedule(plan.INVERSE))
 
     def apply(f, i):
@@ -225,8 +230,17 @@ def tune(plan: "capi.Plan", n_polys: int, scheds: Optional[Iterable[List[Pass]]]
         host[:, l] = rng.integers(0, q, size=(n_polys, plan.N), dtype=np.uint64)
     x, y = to_device(host), empty(host.shape)
     if scheds is None:
-        fu, fs, nf = _search(plan, x, y, n_polys, iters, 1, verbose)
-        iu, is_, ni = _search(plan, x, y, n_polys, iters, 2, verbose)
+        fu = iu = float("inf")
+        fs = is_ = None
+        nf = ni = 0
+        if direction & 1:
+            fu, fs, nf = _search(plan, lambda sc: time_schedule(plan, sc, x, y, n_polys, iters,
+                                                                1)[0], "fwd", verbose)
+        if direction & 2:
+            iu, is_, ni = _search(plan, lambda sc: time_schedule(plan, sc, x, y, n_polys, iters,
+                                                                 2)[1], "inv", verbose)
+        fs = fs or keep[0]
+        is_ = is_ or keep[1]
         tried = nf + ni
     else:
         results = []
@@ -247,6 +261,66 @@ def tune(plan: "capi.Plan", n_polys: int, scheds: Optional[Iterable[List[Pass]]]
     apply(fs, is_)
     out = {"forward": [list(p) for p in fs], "inverse": [list(p) for p in is_],
            "fwd_us": fu, "inv_us": iu, "tried": tried}
+    if use_cache:
+        with _lock:
+            cache = load_cache()
+            cache[key] = out
+            save_cache(cache)
+    return out
+
+
+def tune_tensor(plan: "capi.Plan", n_ct: int, scalars, iters: int = 5, use_cache: bool = True,
+                verbose: bool = False) -> dict:
+    """Pick the inverse schedule for hx_tensor_fma_inverse on n_ct ciphertext
+    pairs (operands back to back, so the element-wise step can run inside
+    the inverse's first pass) by timing that call itself, apply it to the
+    plan and return {"inverse", "us", "tried"}.  Cached like tune()."""
+    import torch
+    from .tensors import to_device, empty
+    import numpy as np
+
+    name = torch.cuda.get_device_name()
+    key = _key(plan.N, plan.moduli, n_ct, name) + "|tensor_inverse"
+    if use_cache:
+        with _lock:
+            hit = load_cache().get(key)
+        if hit:
+            sch = [tuple(p) for p in hit["inverse"]]
+            if valid(plan, sch):
+                plan.set_schedule(sch, plan.INVERSE)
+                return dict(hit, cached=True)
+    keep_f = plan.schedule(plan.FORWARD)
+    rng = np.random.default_rng(2)
+    shape = (n_ct, plan.n_limbs, plan.N)
+
+    def operand(k, bound_mf):
+        h = np.empty((k,) + shape, dtype=np.uint64)
+        for l, q in enumerate(plan.moduli):
+            h[:, :, l] = rng.integers(0, bound_mf * q, size=(k, n_ct, plan.N), dtype=np.uint64)
+        return to_device(h)
+
+    A, E, R = operand(4, 4), operand(3, 1), empty((3,) + shape)
+    st = torch.cuda.current_stream()
+
+    def timer(sched):
+        plan.set_schedule(sched, plan.BOTH)
+        capi.hx_tensor_fma_inverse(plan, R[0], R[1], R[2], A[0], A[1], A[2], A[3], scalars,
+                                   E[0], E[1], E[2], n_ct, 4, st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(iters):
+            capi.hx_tensor_fma_inverse(plan, R[0], R[1], R[2], A[0], A[1], A[2], A[3], scalars,
+                                       E[0], E[1], E[2], n_ct, 4, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / iters
+
+    us, sch, tried = _search(plan, timer, "tensor_inv", verbose)
+    if sch is None:
+        raise RuntimeError("no valid schedule")
+    plan.set_schedule(keep_f, plan.FORWARD)
+    plan.set_schedule(sch, plan.INVERSE)
+    out = {"inverse": [list(p) for p in sch], "us": us, "tried": tried}
     if use_cache:
         with _lock:
             cache = load_cache()

@@ -1,7 +1,8 @@
 """The benchmark's own timed step (bench.HexStep: autotuned schedules, one
-forward call over the four inputs, the fused tensor/FMA kernel, one inverse
-call over the three outputs) at its full size -- N = 65536, 32 mixed limbs
--- compared element by element with the oracle's ciphertext pipeline."""
+forward call over the four inputs, then the tensor/FMA step fused into the
+inverse transform of the three outputs) at its full size -- N = 65536, 32
+mixed limbs -- compared element by element with the oracle's ciphertext
+pipeline."""
 import numpy as np
 import pytest
 

@@ -54,3 +54,17 @@ def test_tuner_picks_a_valid_schedule_and_caches(hexlib, tmp_path, monkeypatch):
     dy = empty(x.shape)
     capi.hx_ntt_forward(plan, dy, to_device(x), 2, 1, 1)
     np.testing.assert_array_equal(to_host(dy), oracle.ntt_forward(x, MIXED3))
+
+
+def test_tuning_one_direction_keeps_the_other(hexlib, tmp_path, monkeypatch):
+    """tune(direction=forward) and tune_tensor (inverse only) each set only
+    their own schedule, whether they time candidates or hit the cache."""
+    monkeypatch.setattr(tune, "CACHE_PATH", str(tmp_path / "cache.json"))
+    N = 1 << 12
+    s = W.scalars(W.SEED_BASE + 960, 20, MIXED3)
+    for _ in range(2):                                   # timed, then cached
+        plan = capi.Plan(N, MIXED3)
+        f = tune.tune(plan, 4, iters=1, direction=plan.FORWARD)["forward"]
+        inv = tune.tune_tensor(plan, 1, s, iters=1)["inverse"]
+        assert [list(p) for p in plan.schedule(plan.FORWARD)] == f
+        assert [list(p) for p in plan.schedule(plan.INVERSE)] == inv
