@@ -150,9 +150,19 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
     return cudaSuccess;
 }
 
+// The fused pass takes the first inverse pass's shape; a schedule with two
+// polynomials per thread there selects the kernel that computes and
+// transforms all three outputs of a ciphertext in one block.
+static int tensor_npf(const PassCfg& p) { return p.np > 1 ? 3 : 1; }
+
 bool tensor_fusable(const NttCfg& cfg) {
     const PassCfg& p = cfg.pass[cfg.npass - 1];   // the inverse runs this pass first
-    return p.pipe != 1 && p.logGc == 0 && pick_tensor_inv(p.logR, p.K, p.pipe == 2) != nullptr;
+    if (p.pipe == 1 || p.logGc != 0) return false;
+    if (!pick_tensor_inv(p.logR, p.K, p.pipe == 2, tensor_npf(p))) return false;
+    const int logTE = p.logGb + p.K;
+    const size_t smem = (size_t)8 * tensor_npf(p) * padded(1u << logTE) +
+                        (p.pipe == 2 ? 16 * (size_t)staged_twiddles(p.logGb, p.K) : 0);
+    return smem <= 192 * 1024;
 }
 
 cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const uint64_t* A,
@@ -161,7 +171,8 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
     if (!tensor_fusable(cfg)) return cudaErrorNotSupported;
     const int L = plan->logN;
     const PassCfg& p = cfg.pass[cfg.npass - 1];
-    TensorPassKernel k = pick_tensor_inv(p.logR, p.K, p.pipe == 2);
+    const int npf = tensor_npf(p);
+    TensorPassKernel k = pick_tensor_inv(p.logR, p.K, p.pipe == 2, npf);
     PassArgs a;
     a.out = out;
     a.in = nullptr;
@@ -178,7 +189,7 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
     const int logTE = p.logGb + p.K;
     const uint32_t tiles = 1u << (L - logTE);
     const uint32_t threads = 1u << (logTE - p.logR);
-    const size_t smem = (size_t)8 * padded(1u << logTE) +
+    const size_t smem = (size_t)8 * npf * padded(1u << logTE) +
                         (p.pipe == 2 ? 16 * (size_t)staged_twiddles(p.logGb, p.K) : 0);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute((const void*)k,
@@ -199,7 +210,7 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
             t.s[i] = sc;
             t.sp[i] = (uint64_t)(((unsigned __int128)sc << 64) / q);
         }
-        k<<<dim3(tiles * 3 * n_ct, chunk), threads, smem, stream>>>(a, t);
+        k<<<dim3(tiles * (npf == 3 ? 1 : 3) * n_ct, chunk), threads, smem, stream>>>(a, t);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -1,0 +1,116 @@
+// The element-wise ciphertext tensor fused into the first pass of the inverse
+// transform (cross-kernel fusion of the multiply and FMA steps into the NTT,
+// the direction Section 5 of the paper points to).
+//
+// The inverse's first pass is always a row pass that stages its input tile
+// through shared memory.  Here that staging step computes the tile of
+// r_k = (d_k s + e_k) mod q, d0 = A0 B0, d1 = A0 B1 + A1 B0, d2 = A1 B1,
+// straight from the forward outputs A0, A1, B0, B1 and the addend e_k, with
+// the same arithmetic as the element-wise tensor kernel (tensor_d, tensor_r);
+// the pass then runs its Gentleman-Sande rounds on it unchanged.  The three
+// r_k never go to HBM, and the element-wise kernel's launch disappears.
+#pragma once
+#include "ntt_kernels.cuh"
+#include "ntt_tensor.h"
+
+namespace hx {
+
+// NPF = 1: one block per (tile, output k, ciphertext, limb); NPF = 3: one
+// block per (tile, ciphertext, limb) computing all three r_k from one read of
+// the operands and transforming them with shared twiddle loads.
+template <int LOG_R, int K, bool TWS, int NPF>
+__global__ void __launch_bounds__(512) ntt_tensor_inv_kernel(PassArgs a, TensorIn t) {
+    extern __shared__ uint64_t sm[];
+    const uint32_t li = blockIdx.y, limb = t.limb0 + li;
+    const uint32_t G = (NPF == 3 ? 1 : 3) * t.n_ct;
+    const uint32_t g = blockIdx.x % G, tile = blockIdx.x / G;
+    const uint32_t k = NPF == 3 ? 0 : g / t.n_ct, p = g % t.n_ct;
+    const LimbDev lc = a.limbs[limb];
+    const uint64_t S = ((uint64_t)t.n_ct * a.n_limbs) << a.L;   // elements per operand
+    const uint64_t row = ((uint64_t)p * a.n_limbs + limb) << a.L;
+    const uint32_t TE = 1u << (a.logGb + K);
+    TileCtx c;
+    c.gin = nullptr;
+    c.gout = a.out + k * S + row;
+    c.b_base = (uint64_t)tile << a.logGb;
+    c.c_base = 0;
+    c.L = a.L;
+    c.s0 = a.s0;
+    c.logGc = 0;
+    c.logGb = a.logGb;
+    c.w = 0;
+    c.nthreads = TE >> LOG_R;
+    c.out_mf = a.out_mf;
+    c.last = a.last != 0;
+    c.poly_stride = S;
+    c.np_valid = NPF;
+
+    const ulonglong2* tw = lc.inv;
+    if constexpr (TWS) {
+        ulonglong2* tws = reinterpret_cast<ulonglong2*>(sm + NPF * padded(TE));
+        stage_twiddles<K, LOG_R>(tws, tw, c);
+        cp_async_commit();
+        tw = tws;
+    }
+
+    // the tile of r_k, two elements per step (16-byte loads; row passes
+    // cover whole rows, so the tile is contiguous from b_base << K)
+    const uint64_t q = lc.q;
+    const uint32_t mf = t.in_mf;
+    const Barrett br{q, lc.barrett_k, lc.barrett_qm1};
+    const uint64_t s = t.s[li], sp = t.sp[li];
+    const uint64_t base = row + (c.b_base << K);
+    const ulonglong2* A0 = reinterpret_cast<const ulonglong2*>(t.A + base);
+    const ulonglong2* A1 = reinterpret_cast<const ulonglong2*>(t.A + S + base);
+    const ulonglong2* B0 = reinterpret_cast<const ulonglong2*>(t.A + 2 * S + base);
+    const ulonglong2* B1 = reinterpret_cast<const ulonglong2*>(t.A + 3 * S + base);
+    const ulonglong2* E = reinterpret_cast<const ulonglong2*>(t.E + base);
+    const ulonglong2 zero = make_ulonglong2(0, 0);
+    const uint32_t TEP = padded(TE);
+    for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
+        const uint32_t l = 2 * i;
+        const bool need0 = NPF == 3 || k != 2, need1 = NPF == 3 || k != 0;
+        const ulonglong2 x0 = need0 ? __ldg(A0 + i) : zero;
+        const ulonglong2 x1 = need1 ? __ldg(A1 + i) : zero;
+        const ulonglong2 y0 = need0 ? __ldg(B0 + i) : zero;
+        const ulonglong2 y1 = need1 ? __ldg(B1 + i) : zero;
+        const uint64_t a0[2] = {small_mod_rt(x0.x, q, mf), small_mod_rt(x0.y, q, mf)};
+        const uint64_t a1[2] = {small_mod_rt(x1.x, q, mf), small_mod_rt(x1.y, q, mf)};
+        const uint64_t b0[2] = {small_mod_rt(y0.x, q, mf), small_mod_rt(y0.y, q, mf)};
+        const uint64_t b1[2] = {small_mod_rt(y1.x, q, mf), small_mod_rt(y1.y, q, mf)};
+#pragma unroll
+        for (int kk = 0; kk < NPF; ++kk) {
+            const uint32_t kt = NPF == 3 ? kk : k;
+            const ulonglong2 e = __ldg(E + kt * (S / 2) + i);
+            sm[kk * TEP + pad(l)] =   // l even: l and l + 1 share one 16-word row
+                tensor_r(tensor_d(kt, a0[0], a1[0], b0[0], b1[0], br), e.x, s, sp, q);
+            sm[kk * TEP + pad(l) + 1] =
+                tensor_r(tensor_d(kt, a0[1], a1[1], b0[1], b1[1], br), e.y, s, sp, q);
+        }
+    }
+    if constexpr (TWS) cp_async_wait<0>();
+    __syncthreads();
+    if (lc.narrow)
+        ntt_rounds<false, false, uint32_t, 0, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
+    else if (lc.trunc)
+        ntt_rounds<false, false, uint64_t, 1, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
+    else
+        ntt_rounds<false, false, uint64_t, 0, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
+}
+
+template <int LOG_R, bool TWS, int NPF>
+inline TensorPassKernel tensor_k(int K) {
+    switch (K) {
+        case 6: return ntt_tensor_inv_kernel<LOG_R, 6, TWS, NPF>;
+        case 7: return ntt_tensor_inv_kernel<LOG_R, 7, TWS, NPF>;
+        case 8: return ntt_tensor_inv_kernel<LOG_R, 8, TWS, NPF>;
+        case 9: return ntt_tensor_inv_kernel<LOG_R, 9, TWS, NPF>;
+        case 10: return ntt_tensor_inv_kernel<LOG_R, 10, TWS, NPF>;
+        case 11: return ntt_tensor_inv_kernel<LOG_R, 11, TWS, NPF>;
+        case 12: return ntt_tensor_inv_kernel<LOG_R, 12, TWS, NPF>;
+        case 13: return ntt_tensor_inv_kernel<LOG_R, 13, TWS, NPF>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace hx

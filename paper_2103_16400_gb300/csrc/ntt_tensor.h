@@ -23,7 +23,8 @@ struct TensorIn {
 typedef void (*TensorPassKernel)(PassArgs, TensorIn);
 
 // ntt_tensor.cu: the fused first inverse pass for (elements per thread,
-// stages, staged twiddles), nullptr if not in the menu
-TensorPassKernel pick_tensor_inv(int logR, int K, bool tws);
+// stages, staged twiddles, outputs per block: 1 or 3), nullptr if not in
+// the menu
+TensorPassKernel pick_tensor_inv(int logR, int K, bool tws, int npf);
 
 }  // namespace hx
