@@ -97,9 +97,25 @@ int hx_abi_version(void);
  */
 int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli, uint32_t n_limbs,
                    const uint64_t* h_roots);
+
+/* hx_plan_create_cyclic: a plan for the cyclic NTT of Section 2.2,
+ *   NTT(a)_i = sum_j a_j omega^(i j) mod q, omega a primitive N-th root of
+ *   unity, and its inverse InvNTT(x)_i = N^-1 sum_j x_j omega^(-i j) mod q.
+ *   hx_ntt_forward / hx_ntt_inverse (and the ragged batches) on this plan
+ *   give these transforms with the same bit-reversed output (forward) and
+ *   input (inverse) order, mod factors and errors as for negacyclic plans,
+ *   and hx_poly_mul gives the product in Z_q[X] / (X^N - 1).
+ *   h_moduli  primes q = 1 mod N, q < 2^62.
+ *   h_roots   n_limbs primitive N-th roots omega, or NULL for the
+ *             numerically smallest one per modulus; hx_plan_roots returns
+ *             omega for these plans.
+ *   Other arguments, memory and errors as hx_plan_create. */
+int hx_plan_create_cyclic(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli,
+                          uint32_t n_limbs, const uint64_t* h_roots);
 int hx_plan_destroy(hx_plan_t plan);
 
-/* Copies the plan's psi per limb into h_roots_out[n_limbs]. */
+/* Copies the plan's root per limb (psi; omega for cyclic plans) into
+ * h_roots_out[n_limbs]. */
 int hx_plan_roots(hx_plan_t plan, uint64_t* h_roots_out);
 
 /* Plan shape: N, limb count and the device bytes the plan holds. */
@@ -171,6 +187,9 @@ int hx_ntt_inverse_raw(uint64_t* d_ptr, uint64_t N, const uint64_t* h_moduli, ui
  * hx_eltwise_add_mod: r = (a + b) mod q; a, b in [0, q); q in [2, 2^63 - 1]
  *   (Section 3, EltwiseAddMod).
  * hx_eltwise_sub_mod: r = (a - b) mod q; a, b in [0, q); q in [2, 2^63 - 1].
+ * hx_eltwise_negate_mod: r = (q - a) mod q (Section 2, element-wise
+ *   negation b_i = q - a_i, taken mod q so that 0 maps to 0); a in [0, q);
+ *   q in [2, 2^63 - 1]; r may equal a.
  * hx_eltwise_mult_mod: r = (a * b) mod q, a and b in [0, k q) for
  *   k = input_mod_factor in {1, 2, 4}; q in [2, 2^62) with k q < 2^63
  *   (Section 3.3, Algorithm "VectorVectorModMulAVX512Int": Barrett reduction
@@ -188,6 +207,9 @@ int hx_eltwise_add_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* 
 int hx_eltwise_sub_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* d_b, uint64_t n,
                        const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
                        hx_stream_t stream);
+int hx_eltwise_negate_mod(uint64_t* d_result, const uint64_t* d_a, uint64_t n,
+                          const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
+                          hx_stream_t stream);
 int hx_eltwise_mult_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* d_b, uint64_t n,
                         const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
                         uint32_t input_mod_factor, hx_stream_t stream);

@@ -1,4 +1,5 @@
-"""CPU oracle for the negacyclic NTT and the element-wise modular kernels.
+"""CPU oracle for the negacyclic NTT, the cyclic NTT and the element-wise
+modular kernels.
 
 TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg are the only callers.  The CUDA library never
@@ -9,7 +10,10 @@ Two layers:
   * ``hx_oracle.c``: plain C with the naive 128-bit ``%`` modular product of
     Listing 1 (Section 2.1); radix-2 Cooley-Tukey forward and Gentleman-Sande
     inverse exactly as the paper's two NTT algorithms state them (Section 2.2);
-    closed-form and schoolbook evaluators; element-wise definitions.
+    closed-form and schoolbook evaluators; element-wise definitions
+    (addition, subtraction, negation, products, FMA); the cyclic NTT, its
+    inverse and the cyclic product written out from their Section 2.2
+    definitions.
   * ``oracle.bigint``: pure-Python big-integer definitions for tiny N, written
     from the definitions alone (no transform algorithm), used to pin the C code.
 
@@ -83,6 +87,16 @@ def lib():
                 getattr(L, name).argtypes = [P64, P64, P64, U64, U64]
             L.oracle_eltwise_fma_mod.restype = None
             L.oracle_eltwise_fma_mod.argtypes = [P64, P64, U64, P64, U64, U64]
+            L.oracle_eltwise_negate_mod.restype = None
+            L.oracle_eltwise_negate_mod.argtypes = [P64, P64, U64, U64]
+            L.oracle_min_primitive_nth_root.restype = U64
+            L.oracle_min_primitive_nth_root.argtypes = [U64, U64]
+            L.oracle_cyclic_ntt_direct.restype = None
+            L.oracle_cyclic_ntt_direct.argtypes = [P64, U64, U64, U64, P64, U64, P64]
+            L.oracle_cyclic_intt_direct.restype = None
+            L.oracle_cyclic_intt_direct.argtypes = [P64, U64, U64, U64, P64]
+            L.oracle_cyclic_schoolbook.restype = None
+            L.oracle_cyclic_schoolbook.argtypes = [P64, P64, U64, U64, P64, U64, P64]
             _lib = L
     return _lib
 
@@ -114,6 +128,11 @@ def is_prime(n: int) -> bool:
 def min_primitive_root(N: int, q: int) -> int:
     """Smallest primitive 2N-th root of unity mod q (0 if none / bad input)."""
     return int(lib().oracle_min_primitive_root(N, q))
+
+
+def min_primitive_nth_root(N: int, q: int) -> int:
+    """Smallest primitive N-th root of unity mod q (0 if none / bad input)."""
+    return int(lib().oracle_min_primitive_nth_root(N, q))
 
 
 def bitrev_powers(N: int, q: int, root: int) -> np.ndarray:
@@ -221,6 +240,49 @@ def eltwise_fma_mod_1(a, s: int, d, q):
     return c
 
 
+def eltwise_negate_mod_1(a, q):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    c = np.empty_like(a)
+    lib().oracle_eltwise_negate_mod(_p(c), _p(a), len(a), q)
+    return c
+
+
+def cyclic_ntt_1(x: np.ndarray, q: int, omega: int, idx: Optional[Sequence[int]] = None):
+    """Cyclic NTT by definition (Section 2.2), natural order: outputs i in idx
+    (all N when idx is None), O(N) each."""
+    a = np.ascontiguousarray(x, dtype=np.uint64)
+    N = len(a)
+    ix = np.arange(N, dtype=np.uint64) if idx is None else \
+        np.ascontiguousarray(np.asarray(idx, dtype=np.uint64))
+    out = np.empty(len(ix), dtype=np.uint64)
+    lib().oracle_cyclic_ntt_direct(_p(a), N, q, omega, _p(ix), len(ix), _p(out))
+    return out
+
+
+def cyclic_intt_1(x: np.ndarray, q: int, omega: int) -> np.ndarray:
+    """Inverse cyclic NTT by definition (Section 2.2), natural order, O(N^2)."""
+    a = np.ascontiguousarray(x, dtype=np.uint64)
+    out = np.empty_like(a)
+    lib().oracle_cyclic_intt_direct(_p(a), len(a), q, omega, _p(out))
+    return out
+
+
+def cyclic_schoolbook(a: np.ndarray, b: np.ndarray, q: int,
+                      idx: Optional[Sequence[int]] = None) -> np.ndarray:
+    """Product in Z_q[X] / (X^N - 1), O(N) per output (all if idx is None)."""
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    N = len(a)
+    if idx is None:
+        out = np.empty(N, dtype=np.uint64)
+        lib().oracle_cyclic_schoolbook(_p(a), _p(b), N, q, None, 0, _p(out))
+    else:
+        ix = np.ascontiguousarray(np.asarray(idx, dtype=np.uint64))
+        out = np.empty(len(ix), dtype=np.uint64)
+        lib().oracle_cyclic_schoolbook(_p(a), _p(b), N, q, _p(ix), len(ix), _p(out))
+    return out
+
+
 # ---------------------------------------------------------------- batches
 # Arrays are [n_polys, n_limbs, N]; limb l is reduced modulo moduli[l].
 def ntt_forward(x: np.ndarray, moduli: Sequence[int], psis: Optional[Sequence[int]] = None):
@@ -244,6 +306,14 @@ def eltwise_add_mod(a, b, moduli):
     for p in range(a.shape[0]):
         for l, q in enumerate(moduli):
             out[p, l] = eltwise_add_mod_1(a[p, l], b[p, l], int(q))
+    return out
+
+
+def eltwise_negate_mod(a, moduli):
+    out = np.empty_like(a)
+    for p in range(a.shape[0]):
+        for l, q in enumerate(moduli):
+            out[p, l] = eltwise_negate_mod_1(a[p, l], int(q))
     return out
 
 

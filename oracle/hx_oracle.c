@@ -1,6 +1,6 @@
 /*
- * Plain, slow CPU oracle for the negacyclic NTT and the element-wise modular
- * kernels of Intel HEXL (arXiv 2103.16400).
+ * Plain, slow CPU oracle for the negacyclic NTT, the cyclic NTT and the
+ * element-wise modular kernels of Intel HEXL (arXiv 2103.16400).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline leg may load this library.  It shares no code,
@@ -20,6 +20,10 @@
  *  - The 2N-th root psi, when the caller gives none, is the numerically
  *    smallest primitive 2N-th root of unity mod q.
  *  - psi_rev[0] is never read by the transform; it is stored as 1.
+ *  - Element-wise negation b_i = q - a_i (Section 2) is read as (q - a_i) mod q,
+ *    so that a_i = 0 gives 0, inside Z_q.
+ *  - The cyclic NTT's N-th root omega, when the caller gives none, is the
+ *    numerically smallest primitive N-th root of unity mod q.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -256,5 +260,87 @@ void oracle_eltwise_fma_mod(uint64_t* c, const uint64_t* a, uint64_t s, const ui
     for (uint64_t i = 0; i < n; i++) {
         uint64_t p = oracle_mulmod(a[i], s, q);
         c[i] = d ? oracle_addmod(p, d[i], q) : p;
+    }
+}
+
+/* c_i = (q - a_i) mod q: element-wise negation (Section 2) */
+void oracle_eltwise_negate_mod(uint64_t* c, const uint64_t* a, uint64_t n, uint64_t q) {
+    for (uint64_t i = 0; i < n; i++) c[i] = oracle_submod(0, a[i], q);
+}
+
+/* ---- cyclic NTT (Section 2.2 definitions) ------------------------------- */
+
+/*
+ * The numerically smallest primitive N-th root of unity mod q (N a power of
+ * two >= 2, q prime, q = 1 mod N): x is primitive exactly when x^(N/2) = -1.
+ * Take g = 2, 3, ... until h = g^((q-1)/N) satisfies h^(N/2) = -1; the
+ * primitive roots are h^k for odd k < N.  Returns 0 if the preconditions fail.
+ */
+uint64_t oracle_min_primitive_nth_root(uint64_t N, uint64_t q) {
+    if (N < 2 || (N & (N - 1)) || q < 3 || (q - 1) % N != 0) return 0;
+    if (!oracle_is_prime(q)) return 0;
+    uint64_t h = 0;
+    for (uint64_t g = 2; g < q && g < (1ULL << 24); g++) {
+        uint64_t c = oracle_powmod(g, (q - 1) / N, q);
+        if (oracle_powmod(c, N / 2, q) == q - 1) { h = c; break; }
+    }
+    if (h == 0) return 0;
+    uint64_t h2 = oracle_mulmod(h, h, q);
+    uint64_t x = h, best = h;
+    for (uint64_t k = 1; k < N / 2; k++) {
+        x = oracle_mulmod(x, h2, q);
+        if (x < best) best = x;
+    }
+    return best;
+}
+
+/*
+ * Forward cyclic NTT by its definition, natural order, for selected outputs:
+ * out[k] = sum_j a_j omega^(i j) mod q with i = idx[k].  O(N) per output.
+ */
+void oracle_cyclic_ntt_direct(const uint64_t* a, uint64_t N, uint64_t q, uint64_t omega,
+                              const uint64_t* idx, uint64_t n_idx, uint64_t* out) {
+    for (uint64_t k = 0; k < n_idx; k++) {
+        uint64_t r = oracle_powmod(omega, idx[k] % N, q);
+        uint64_t acc = 0, p = 1 % q;
+        for (uint64_t j = 0; j < N; j++) {
+            acc = oracle_addmod(acc, oracle_mulmod(a[j] % q, p, q), q);
+            p = oracle_mulmod(p, r, q);
+        }
+        out[k] = acc;
+    }
+}
+
+/*
+ * Inverse cyclic NTT by its definition, natural order, all outputs:
+ * b_i = N^-1 sum_j x_j omega^(-i j) mod q.  O(N^2).
+ */
+void oracle_cyclic_intt_direct(const uint64_t* x, uint64_t N, uint64_t q, uint64_t omega,
+                               uint64_t* b) {
+    uint64_t winv = oracle_invmod(omega, q), ninv = oracle_invmod(N % q, q);
+    for (uint64_t i = 0; i < N; i++) {
+        uint64_t r = oracle_powmod(winv, i, q);
+        uint64_t acc = 0, p = 1 % q;
+        for (uint64_t j = 0; j < N; j++) {
+            acc = oracle_addmod(acc, oracle_mulmod(x[j] % q, p, q), q);
+            p = oracle_mulmod(p, r, q);
+        }
+        b[i] = oracle_mulmod(acc, ninv, q);
+    }
+}
+
+/*
+ * Cyclic schoolbook product in Z_q[X] / (X^N - 1), selected outputs (all
+ * when idx is NULL): c_i = sum_j a_j b_((i - j) mod N) mod q.  O(N) each.
+ */
+void oracle_cyclic_schoolbook(const uint64_t* a, const uint64_t* b, uint64_t N, uint64_t q,
+                              const uint64_t* idx, uint64_t n_idx, uint64_t* out) {
+    uint64_t count = idx ? n_idx : N;
+    for (uint64_t k = 0; k < count; k++) {
+        uint64_t i = idx ? idx[k] : k;
+        uint64_t acc = 0;
+        for (uint64_t j = 0; j < N; j++)
+            acc = oracle_addmod(acc, oracle_mulmod(a[j] % q, b[(i + N - j) % N] % q, q), q);
+        out[k] = acc;
     }
 }

@@ -25,6 +25,7 @@ _SIGS = {
     "hx_strerror": [I32],
     "hx_abi_version": [],
     "hx_plan_create": [ctypes.POINTER(VP), U64, P64, U32, P64],
+    "hx_plan_create_cyclic": [ctypes.POINTER(VP), U64, P64, U32, P64],
     "hx_plan_destroy": [VP],
     "hx_plan_roots": [VP, P64],
     "hx_plan_info": [VP, P64, ctypes.POINTER(U32), P64],
@@ -36,6 +37,7 @@ _SIGS = {
     "hx_ntt_inverse_raw": [VP, U64, P64, U32, U32, U32, VP],
     "hx_eltwise_add_mod": [VP, VP, VP, U64, P64, U32, U32, VP],
     "hx_eltwise_sub_mod": [VP, VP, VP, U64, P64, U32, U32, VP],
+    "hx_eltwise_negate_mod": [VP, VP, U64, P64, U32, U32, VP],
     "hx_eltwise_mult_mod": [VP, VP, VP, U64, P64, U32, U32, U32, VP],
     "hx_eltwise_fma_mod": [VP, VP, P64, VP, U64, P64, U32, U32, U32, VP],
     "hx_poly_mul": [VP, VP, VP, VP, U32, VP],
@@ -121,15 +123,20 @@ def _stream(stream) -> Optional[int]:
 
 # --------------------------------------------------------------------- plans
 class Plan:
-    """Owns an hx_plan_t: device twiddle tables for (N, moduli)."""
+    """Owns an hx_plan_t: device twiddle tables for (N, moduli); negacyclic
+    (roots psi of order 2N), or with cyclic=True the cyclic NTT (roots omega
+    of order N)."""
 
-    def __init__(self, N: int, moduli: Sequence[int], roots: Optional[Sequence[int]] = None):
+    def __init__(self, N: int, moduli: Sequence[int], roots: Optional[Sequence[int]] = None,
+                 cyclic: bool = False):
         L = load()
         h = VP()
         mod = host_u64(moduli)
         rts = host_u64(roots) if roots is not None else None
-        _check("hx_plan_create", L.hx_plan_create(ctypes.byref(h), N, mod, len(moduli), rts))
+        fn = "hx_plan_create_cyclic" if cyclic else "hx_plan_create"
+        _check(fn, getattr(L, fn)(ctypes.byref(h), N, mod, len(moduli), rts))
         self.handle = h.value
+        self.cyclic = cyclic
         self.N = N
         self.moduli = [int(q) for q in moduli]
         self.n_limbs = len(moduli)
@@ -297,6 +304,11 @@ def hx_eltwise_add_mod(result, a, b, n: int, moduli, n_polys: int = 1, stream=No
 def hx_eltwise_sub_mod(result, a, b, n: int, moduli, n_polys: int = 1, stream=None):
     _check("hx_eltwise_sub_mod", load().hx_eltwise_sub_mod(
         ptr(result), ptr(a), ptr(b), n, host_u64(moduli), len(moduli), n_polys, _stream(stream)))
+
+
+def hx_eltwise_negate_mod(result, a, n: int, moduli, n_polys: int = 1, stream=None):
+    _check("hx_eltwise_negate_mod", load().hx_eltwise_negate_mod(
+        ptr(result), ptr(a), n, host_u64(moduli), len(moduli), n_polys, _stream(stream)))
 
 
 def hx_eltwise_mult_mod(result, a, b, n: int, moduli, n_polys: int = 1,

@@ -171,6 +171,15 @@ int hx_eltwise_sub_mod(uint64_t* r, const uint64_t* a, const uint64_t* b, uint64
                                       (cudaStream_t)stream));
 }
 
+int hx_eltwise_negate_mod(uint64_t* r, const uint64_t* a, uint64_t n, const uint64_t* h_moduli,
+                          uint32_t n_limbs, uint32_t n_polys, hx_stream_t stream) {
+    int st = check_elt(r, a, nullptr, false, n, h_moduli, n_limbs, n_polys);
+    if (st != HX_OK) return st;
+    if ((st = check_moduli(h_moduli, n_limbs, (1ull << 63) - 1, 2)) != HX_OK) return st;
+    return cuda_status(launch_eltwise(ELT_NEG, r, a, nullptr, nullptr, n, h_moduli, n_limbs,
+                                      n_polys, 1, (cudaStream_t)stream));
+}
+
 int hx_eltwise_mult_mod(uint64_t* r, const uint64_t* a, const uint64_t* b, uint64_t n,
                         const uint64_t* h_moduli, uint32_t n_limbs, uint32_t n_polys,
                         uint32_t in_mf, hx_stream_t stream) {

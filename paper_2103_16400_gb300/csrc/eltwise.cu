@@ -1,6 +1,7 @@
 // Element-wise modular kernels (Section 3 free-function API, Section 3.3).
 //
 //   add / sub : (a +- b) mod q, inputs in [0, q)                  EltwiseAddMod
+//   negate    : (q - a) mod q, input in [0, q)       element-wise negation
 //   mult      : (a * b) mod q by Barrett with Q = bitlen(q),
 //               L = 63 + Q, k = floor(2^L / q)  (Algorithm
 //               "VectorVectorModMulAVX512Int"; inputs first reduced from
@@ -57,6 +58,8 @@ __device__ __forceinline__ uint64_t elt_apply(uint64_t a, uint64_t b, const EltC
         return r >= q ? r - q : r;
     } else if (OP == ELT_SUB) {
         return a >= b ? a - b : a + (q - b);
+    } else if (OP == ELT_NEG) {
+        return a == 0 ? 0 : q - a;
     } else if (OP == ELT_MULT) {
         a = small_mod<INMF>(a, q);
         b = small_mod<INMF>(b, q);
@@ -200,6 +203,7 @@ cudaError_t launch_eltwise(int op, uint64_t* r, const uint64_t* a, const uint64_
         switch (op) {
             case ELT_ADD: e = launch_one<ELT_ADD, 1, false>(r, a, b, c, g, n_polys, stream); break;
             case ELT_SUB: e = launch_one<ELT_SUB, 1, false>(r, a, b, c, g, n_polys, stream); break;
+            case ELT_NEG: e = launch_one<ELT_NEG, 1, false>(r, a, b, c, g, n_polys, stream); break;
             case ELT_MULT: e = dispatch_mf<ELT_MULT, false>(in_mf, r, a, b, c, g, n_polys, stream); break;
             case ELT_FMA:
                 e = b ? dispatch_mf<ELT_FMA, true>(in_mf, r, a, b, c, g, n_polys, stream)

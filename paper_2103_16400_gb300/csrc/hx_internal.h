@@ -63,6 +63,7 @@ struct hx_plan_s {
     hx::LimbDev* d_limbs = nullptr;
     std::vector<hx::LimbDev> h_limbs;
     uint64_t device_bytes = 0;
+    bool cyclic = false;               // cyclic NTT over omega (else negacyclic over psi)
     hx::NttCfg cfg_fwd{}, cfg_inv{};   // kernel schedules per direction
 };
 
@@ -75,9 +76,10 @@ void count_launch(uint64_t n = 1);
 bool is_prime_u64(uint64_t n);
 uint64_t powmod_u64(uint64_t a, uint64_t e, uint64_t q);
 uint64_t min_primitive_root(uint64_t N, uint64_t q);
+uint64_t min_primitive_nth_root(uint64_t N, uint64_t q);
 NttCfg default_cfg(int logN, bool forward);
 int acquire_tables(int device, uint64_t N, int logN, const std::vector<uint64_t>& moduli,
-                   const std::vector<uint64_t>& roots,
+                   const std::vector<uint64_t>& roots, bool cyclic,
                    std::vector<std::shared_ptr<TableEntry>>* out);
 
 // ntt.cu
@@ -95,7 +97,7 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
                                   uint32_t in_mf, const NttCfg& cfg, cudaStream_t stream);
 
 // eltwise.cu
-enum EltOp { ELT_ADD = 0, ELT_SUB = 1, ELT_MULT = 2, ELT_FMA = 3 };
+enum EltOp { ELT_ADD = 0, ELT_SUB = 1, ELT_MULT = 2, ELT_FMA = 3, ELT_NEG = 4 };
 cudaError_t launch_eltwise(int op, uint64_t* r, const uint64_t* a, const uint64_t* b,
                            const uint64_t* h_scalars, uint64_t n, const uint64_t* h_moduli,
                            uint32_t n_limbs, uint32_t n_polys, uint32_t in_mf,

@@ -7,6 +7,12 @@
 //   inv[k] = {psi^-brv(k), floor(psi^-brv(k) * beta / q)}  Gentleman-Sande twiddles
 // with beta = 2^64 for wide limbs and 2^32 for narrow limbs (q < 2^30), the
 // Shoup factor W' of the Harvey butterflies.  Entry 0 is never read; it holds 1.
+//
+// Cyclic plans (the cyclic NTT of Section 2.2, over a primitive N-th root
+// omega) use the same transforms with the twist removed: for k = 2^s + i,
+// i < 2^s, the negacyclic entry psi^brv(k) = psi^(N/2^(s+1)) (psi^2)^(brv_s(i)
+// N/2^(s+1)) becomes omega^(brv_s(i) N/2^(s+1)).  The same butterfly loops
+// then give the cyclic NTT in bit-reversed order and its inverse.
 #include <string.h>
 
 #include <algorithm>
@@ -76,6 +82,25 @@ uint64_t min_primitive_root(uint64_t N, uint64_t q) {
     return best;
 }
 
+// Smallest primitive N-th root of unity mod prime q = 1 mod N (N a power of
+// two >= 2): x has order N exactly when x^(N/2) = -1; h = g^((q-1)/N) for a
+// quadratic non-residue g has that property, and the primitive N-th roots are
+// the odd powers of h.
+uint64_t min_primitive_nth_root(uint64_t N, uint64_t q) {
+    uint64_t h = 0;
+    for (uint64_t g = 2; g < q && g < (1ull << 24); ++g) {
+        uint64_t c = powmod_u64(g, (q - 1) / N, q);
+        if (powmod_u64(c, N / 2, q) == q - 1) { h = c; break; }
+    }
+    if (!h) return 0;
+    uint64_t h2 = mulmod(h, h, q), x = h, best = h;
+    for (uint64_t k = 1; k < N / 2; ++k) {
+        x = mulmod(x, h2, q);
+        best = std::min(best, x);
+    }
+    return best;
+}
+
 static inline uint64_t bitrev(uint64_t i, int logn) {
     uint64_t r = 0;
     for (int b = 0; b < logn; ++b) { r = (r << 1) | (i & 1); i >>= 1; }
@@ -86,19 +111,27 @@ static inline uint64_t shoup(uint64_t w, uint64_t q, bool narrow) {
     return narrow ? (uint64_t)(((uint64_t)w << 32) / q) : (uint64_t)(((u128)w << 64) / q);
 }
 
-// Fill one limb's tables (host staging buffers of N pairs each).
-static void fill_limb(uint64_t N, int logN, uint64_t q, uint64_t psi, ulonglong2* fwd,
-                      ulonglong2* inv, LimbDev* ld) {
+// Fill one limb's tables (host staging buffers of N pairs each); `root` is
+// psi (negacyclic) or omega (cyclic).
+static void fill_limb(uint64_t N, int logN, uint64_t q, uint64_t root, bool cyclic,
+                      ulonglong2* fwd, ulonglong2* inv, LimbDev* ld) {
     const bool narrow = q < (1ull << 30);
-    const uint64_t psi_inv = powmod_u64(psi, q - 2, q);
+    const uint64_t root_inv = powmod_u64(root, q - 2, q);
     std::vector<uint64_t> pw(N), pwi(N);
     pw[0] = pwi[0] = 1;
     for (uint64_t i = 1; i < N; ++i) {
-        pw[i] = mulmod(pw[i - 1], psi, q);
-        pwi[i] = mulmod(pwi[i - 1], psi_inv, q);
+        pw[i] = mulmod(pw[i - 1], root, q);
+        pwi[i] = mulmod(pwi[i - 1], root_inv, q);
     }
     for (uint64_t k = 0; k < N; ++k) {
-        uint64_t r = bitrev(k, logN);
+        uint64_t r;
+        if (!cyclic) {
+            r = bitrev(k, logN);
+        } else {
+            int sb = 0;
+            while (k >> (sb + 1)) ++sb;   // k = 2^sb + i
+            r = k ? bitrev(k - (1ull << sb), sb) << (logN - 1 - sb) : 0;
+        }
         uint64_t w = k ? pw[r] : 1, wi = k ? pwi[r] : 1;
         fwd[k] = make_ulonglong2(w, shoup(w, q, narrow));
         inv[k] = make_ulonglong2(wi, shoup(wi, q, narrow));
@@ -160,8 +193,10 @@ std::mutex g_table_mu;
 std::map<TableKey, std::weak_ptr<TableEntry>> g_tables;
 }  // namespace
 
+// (device, N, q, root) identifies a table: a cyclic plan's omega has order N,
+// a negacyclic plan's psi order 2N, so the two kinds never share a key.
 int acquire_tables(int device, uint64_t N, int logN, const std::vector<uint64_t>& moduli,
-                   const std::vector<uint64_t>& roots,
+                   const std::vector<uint64_t>& roots, bool cyclic,
                    std::vector<std::shared_ptr<TableEntry>>* out) {
     std::lock_guard<std::mutex> g(g_table_mu);
     const size_t L = moduli.size();
@@ -188,7 +223,8 @@ int acquire_tables(int device, uint64_t N, int logN, const std::vector<uint64_t>
             for (size_t m = t; m < missing.size(); m += nthreads) {
                 const size_t l = missing[m];
                 host[m].resize(2 * N);
-                fill_limb(N, logN, moduli[l], roots[l], host[m].data(), host[m].data() + N, &lds[m]);
+                fill_limb(N, logN, moduli[l], roots[l], cyclic, host[m].data(),
+                          host[m].data() + N, &lds[m]);
             }
         });
     }
@@ -231,25 +267,28 @@ int acquire_tables(int device, uint64_t N, int logN, const std::vector<uint64_t>
 
 using namespace hx;
 
-extern "C" int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli,
-                              uint32_t n_limbs, const uint64_t* h_roots) {
+// Plan creation for both kinds: negacyclic (roots psi of order 2N, q = 1
+// mod 2N) and cyclic (roots omega of order N, q = 1 mod N).
+static int plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli, uint32_t n_limbs,
+                       const uint64_t* h_roots, bool cyclic) {
     if (!out || !h_moduli) return HX_ERR_NULL;
     *out = nullptr;
     if (N < 1024 || N > (1u << 17) || (N & (N - 1))) return HX_ERR_DEGREE;
     if (n_limbs == 0 || n_limbs > 4096) return HX_ERR_ARG;
     int logN = 0;
     while ((1ull << logN) < N) ++logN;
+    const uint64_t order = cyclic ? N : 2 * N;   // order of the root
     std::vector<uint64_t> roots(n_limbs);
     for (uint32_t l = 0; l < n_limbs; ++l) {
         uint64_t q = h_moduli[l];
-        if (q < 3 || q >= (1ull << 62) || (q - 1) % (2 * N) != 0 || !is_prime_u64(q))
+        if (q < 3 || q >= (1ull << 62) || (q - 1) % order != 0 || !is_prime_u64(q))
             return HX_ERR_MODULUS;
         if (h_roots) {
             uint64_t r = h_roots[l];
-            if (r == 0 || r >= q || powmod_u64(r, N, q) != q - 1) return HX_ERR_ROOT;
+            if (r == 0 || r >= q || powmod_u64(r, order / 2, q) != q - 1) return HX_ERR_ROOT;
             roots[l] = r;
         } else {
-            roots[l] = min_primitive_root(N, q);
+            roots[l] = cyclic ? min_primitive_nth_root(N, q) : min_primitive_root(N, q);
             if (!roots[l]) return HX_ERR_MODULUS;
         }
     }
@@ -258,12 +297,13 @@ extern "C" int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_modu
     p->N = N;
     p->logN = logN;
     p->n_limbs = n_limbs;
+    p->cyclic = cyclic;
     p->moduli.assign(h_moduli, h_moduli + n_limbs);
     p->roots = roots;
     p->cfg_fwd = default_cfg(logN, true);
     p->cfg_inv = default_cfg(logN, false);
     cudaGetDevice(&p->device);
-    int st = acquire_tables(p->device, N, logN, p->moduli, roots, &p->tables);
+    int st = acquire_tables(p->device, N, logN, p->moduli, roots, cyclic, &p->tables);
     if (st != HX_OK) {
         delete p;
         return st;
@@ -290,6 +330,16 @@ extern "C" int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_modu
     }
     *out = p;
     return HX_OK;
+}
+
+extern "C" int hx_plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli,
+                              uint32_t n_limbs, const uint64_t* h_roots) {
+    return plan_create(out, N, h_moduli, n_limbs, h_roots, false);
+}
+
+extern "C" int hx_plan_create_cyclic(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli,
+                                     uint32_t n_limbs, const uint64_t* h_roots) {
+    return plan_create(out, N, h_moduli, n_limbs, h_roots, true);
 }
 
 extern "C" int hx_plan_destroy(hx_plan_t p) {

@@ -170,3 +170,17 @@ def test_dyadic_tensor_fma_lazy_inputs(hexlib):
     d = [M(a0, b0), oracle.eltwise_add_mod(M(a0, b1), M(a1, b0), qs), M(a1, b1)]
     for o, dk, ek in zip(outs, d, E):
         np.testing.assert_array_equal(to_host(o), oracle.eltwise_fma_mod(dk, s, ek, qs))
+
+
+@pytest.mark.parametrize("n,n_polys,moduli", ELT_CASES)
+def test_negate(hexlib, n, n_polys, moduli):
+    """(q - a) mod q, with zeros planted (they must stay 0), out of place and
+    in place."""
+    a = rows(1, 3, n_polys, moduli, n)
+    a[:, :, ::5] = 0
+    exp = oracle.eltwise_negate_mod(a, moduli)
+    da, dr = to_device(a), empty(a.shape)
+    capi.hx_eltwise_negate_mod(dr, da, n, moduli, n_polys)
+    np.testing.assert_array_equal(to_host(dr), exp)
+    capi.hx_eltwise_negate_mod(da, da, n, moduli, n_polys)
+    np.testing.assert_array_equal(to_host(da), exp)

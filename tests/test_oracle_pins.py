@@ -297,3 +297,92 @@ def test_pins_catch_planted_mistakes():
     assert not np.array_equal(wrong_inv, arr)
     bad = T.psi_rev.copy(); bad[1:] = T.psi_rev[::-1][:-1]                 # reversed table
     assert [int(x) for x in oracle.ntt_forward_1(arr, q, psi_rev=bad)] != ref
+
+
+# ---------------------------------------------------------------- negation
+def test_negate_against_definition_and_invariants():
+    """(q - a) mod q: 0 stays 0; a + (-a) = 0 and -(-a) = a through the
+    oracle's own addition; values match Python integers."""
+    for q in BIG_Q + [3, 97]:
+        a = np.concatenate([np.array([0, 1, q - 1, q // 2], dtype=np.uint64),
+                            _rand(500, q, 41)])
+        na = oracle.eltwise_negate_mod_1(a, q)
+        assert [int(x) for x in na] == [(q - int(x)) % q for x in a]
+        assert int(na[0]) == 0 and int(na[2]) == 1
+        assert not oracle.eltwise_add_mod_1(a, na, q).any()
+        np.testing.assert_array_equal(oracle.eltwise_negate_mod_1(na, q), a)
+
+
+# ---------------------------------------------------------------- cyclic NTT
+CYC = [(2, 3), (4, 5), (8, 17), (16, 97), (32, 97), (64, 193), (128, 257), (256, 7681)]
+
+
+@pytest.mark.parametrize("N,q", CYC)
+def test_min_nth_root_exhaustive(N, q):
+    """Against a brute-force search over Z_q for elements of order exactly N."""
+    order_n = [x for x in range(1, q) if pow(x, N, q) == 1 and
+               all(pow(x, d, q) != 1 for d in sympy.divisors(N) if d < N)]
+    assert oracle.min_primitive_nth_root(N, q) == min(order_n)
+
+
+def test_min_nth_root_rejects_bad_inputs():
+    assert oracle.min_primitive_nth_root(16, 96) == 0      # not prime
+    assert oracle.min_primitive_nth_root(16, 23) == 0      # 16 does not divide 22
+    assert oracle.min_primitive_nth_root(12, 13) == 0      # N not a power of two
+
+
+@pytest.mark.parametrize("N,q", CYC[2:])
+def test_cyclic_special_inputs(N, q):
+    """NTT(delta_0) = all ones, NTT(all ones) = N delta_0 (the geometric sums
+    of a primitive N-th root vanish), NTT(X) = (omega^i)_i."""
+    w = oracle.min_primitive_nth_root(N, q)
+    delta = np.zeros(N, dtype=np.uint64); delta[0] = 1
+    assert (oracle.cyclic_ntt_1(delta, q, w) == 1).all()
+    ones = np.ones(N, dtype=np.uint64)
+    got = oracle.cyclic_ntt_1(ones, q, w)
+    assert int(got[0]) == N % q and not got[1:].any()
+    x = np.zeros(N, dtype=np.uint64); x[1] = 1
+    assert [int(v) for v in oracle.cyclic_ntt_1(x, q, w)] == [pow(w, i, q) for i in range(N)]
+
+
+@pytest.mark.parametrize("N,q", [(64, 193), (256, 7681), (1024, 562949953443841),
+                                 (512, 576460752308273153)])
+def test_cyclic_inverse_and_convolution_theorem(N, q):
+    """InvNTT(NTT(a)) = a, and InvNTT(NTT(a) . NTT(b)) is the product in
+    Z_q[X] / (X^N - 1) (Section 2.2), against the cyclic schoolbook."""
+    w = oracle.min_primitive_nth_root(N, q)
+    a, b = _rand(N, q, 51), _rand(N, q, 52)
+    fa, fb = oracle.cyclic_ntt_1(a, q, w), oracle.cyclic_ntt_1(b, q, w)
+    np.testing.assert_array_equal(oracle.cyclic_intt_1(fa, q, w), a)
+    prod = oracle.cyclic_intt_1(oracle.eltwise_mult_mod_1(fa, fb, q), q, w)
+    np.testing.assert_array_equal(prod, oracle.cyclic_schoolbook(a, b, q))
+
+
+def test_cyclic_schoolbook_monomial_is_rotation():
+    """a * X^k in Z_q[X] / (X^N - 1) rotates the coefficients, with no sign
+    change (unlike the negacyclic ring)."""
+    N, q = 128, 7681
+    a = _rand(N, q, 53)
+    for k in (0, 1, 5, 127):
+        x = np.zeros(N, dtype=np.uint64); x[k] = 1
+        np.testing.assert_array_equal(oracle.cyclic_schoolbook(a, x, q), np.roll(a, k))
+
+
+@pytest.mark.parametrize("N,q", [(16, 97), (256, 7681), (1024, 562949953443841)])
+def test_cyclic_is_the_untwisted_negacyclic(N, q):
+    """With psi a primitive 2N-th root and omega = psi^2, the cyclic NTT of a
+    read in bit-reversed order equals the (separately pinned) negacyclic NTT
+    of the twisted input a_j psi^-j."""
+    psi = oracle.min_primitive_root(N, q)
+    w = psi * psi % q
+    a = _rand(N, q, 54)
+    pinv = oracle.invmod(psi, q)
+    tw = np.array([int(a[j]) * pow(pinv, j, q) % q for j in range(N)], dtype=np.uint64)
+    neg = oracle.ntt_forward_1(tw, q, psi)
+    cyc = oracle.cyclic_ntt_1(a, q, w)
+    logn = N.bit_length() - 1
+    brv = [int(format(i, f"0{logn}b")[::-1], 2) for i in range(N)]
+    np.testing.assert_array_equal(neg, cyc[brv])
+    # planted mistakes: the inverse root, or a root of order N/2, break it
+    assert not np.array_equal(neg, oracle.cyclic_ntt_1(a, q, oracle.invmod(w, q))[brv])
+    assert not np.array_equal(neg, oracle.cyclic_ntt_1(a, q, w * w % q)[brv])
