@@ -85,6 +85,14 @@ def slots_per_butterfly(q):
     return SLOTS_WIDE_TRUNC if q < (1 << 61) else SLOTS_WIDE
 
 
+#: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, both pass launches)
+#: of one forward call over 4 polynomials x 32 mixed limbs at N = 65536, from one
+#: ncu --set full capture of that call under the schedule below; reported only
+#: when the tuned forward schedule is that one (other kernels, other traffic).
+FWD_TRAFFIC_BYTES = 67246848 + 16910592 + 100663296 + 17612544
+FWD_TRAFFIC_SCHEDULE = [[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]
+
+
 def imad_slots_per_transform(N, moduli):
     """Algorithmic IMAD-pipe slots of one limb-transform: N/2 log2 N Harvey
     butterflies, each one Shoup product."""
@@ -612,8 +620,13 @@ def main():
     alg_slots = 4 * sum(imad_slots_per_transform(N, wl.moduli))
     achieved = alg_slots / (fwd_call_ms * 1e-3)
     fwd_bytes = 4 * 16 * N * nl
+    fwd_sched = getattr(step, "tuned", {}).get("forward", {}).get("forward")
+    traffic = (FWD_TRAFFIC_BYTES if (N, nl) == (1 << 16, 32) and fwd_sched == FWD_TRAFFIC_SCHEDULE
+               else None)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": imad_rate / 1e12,
-                "unit": "T IMAD-slot/s", "frac": achieved / imad_rate, "traffic": None,
+                "unit": "T IMAD-slot/s", "frac": achieved / imad_rate, "traffic": traffic,
+                "traffic_unit": "bytes per forward call (2 launches), ncu",
+                "alg_bytes_per_call": fwd_bytes,
                 "kernel": "hx_ntt_forward, 4 polys x 32 limbs (ntt pass kernels, 2 launches)",
                 "fwd_call_us": fwd_call_ms * 1e3,
                 "alg_slots_per_call": alg_slots,
