@@ -398,6 +398,12 @@ int hx_polymul_ragged(const hx_polymul_item* h_items, uint32_t n_items, void* d_
  *   truncated high word from three partial products, lazy bound 4q, needs
  *   q < 2^61), bit 4 the inverse butterfly.  Returns butterflies per second.
  *   Synchronises `stream`.
+ * hx_probe_copy_rate: copies `bytes` (a multiple of 16, both addresses
+ *   16-byte aligned) from src to dst `iters` times with a grid of
+ *   blocks_per_sm 256-thread blocks per SM doing 16-byte loads and stores;
+ *   either side may be device memory or pinned host memory (reached through
+ *   unified addressing over the CPU-GPU link).  Returns bytes per second
+ *   (one copy's bytes, not read + write) and the per-copy time in *ms.
  * Errors: HX_ERR_NULL, HX_ERR_ARG, HX_ERR_NOMEM, HX_ERR_CUDA.
  */
 uint64_t hx_launch_count(void);
@@ -405,6 +411,9 @@ int hx_probe_int_mul_rate(uint32_t kind, uint32_t iters, double* ops_per_s, floa
                           hx_stream_t stream);
 int hx_probe_butterfly_rate(uint32_t variant, uint32_t iters, uint64_t q,
                             double* butterflies_per_s, float* ms, hx_stream_t stream);
+int hx_probe_copy_rate(void* dst, const void* src, uint64_t bytes, uint32_t iters,
+                       uint32_t blocks_per_sm, double* bytes_per_s, float* ms,
+                       hx_stream_t stream);
 
 #ifdef __cplusplus
 }

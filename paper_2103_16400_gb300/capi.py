@@ -57,6 +57,8 @@ _SIGS = {
                               ctypes.POINTER(ctypes.c_float), VP],
     "hx_probe_butterfly_rate": [U32, U32, U64, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_float), VP],
+    "hx_probe_copy_rate": [VP, VP, U64, U32, U32, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_float), VP],
 }
 _RESTYPES = {"hx_strerror": ctypes.c_char_p, "hx_launch_count": U64}
 
@@ -376,5 +378,16 @@ def hx_probe_butterfly_rate(q: int, variant: int = 1, inverse: bool = False, ite
     r, t = ctypes.c_double(), ctypes.c_float()
     _check("hx_probe_butterfly_rate", load().hx_probe_butterfly_rate(
         variant | (16 if inverse else 0), iters, q, ctypes.byref(r), ctypes.byref(t),
+        _stream(stream)))
+    return r.value, t.value
+
+
+def hx_probe_copy_rate(dst, src, nbytes: int, iters: int = 10, blocks_per_sm: int = 4,
+                       stream=None):
+    """(bytes per second, ms per copy) of the library's 16-byte copy kernel
+    from src to dst (torch tensors; either may be pinned host memory)."""
+    r, t = ctypes.c_double(), ctypes.c_float()
+    _check("hx_probe_copy_rate", load().hx_probe_copy_rate(
+        ptr(dst), ptr(src), nbytes, iters, blocks_per_sm, ctypes.byref(r), ctypes.byref(t),
         _stream(stream)))
     return r.value, t.value

@@ -8,6 +8,10 @@
 // alternating).  The grid fills every SM; the rate is
 // (threads x iterations x 16 instructions) / elapsed time.
 //
+// hx_probe_copy_rate: a 16-byte grid-stride copy between any two addresses
+// the GPU can reach (device memory, or pinned host memory through unified
+// addressing), timed like the others.
+//
 // hx_probe_butterfly_rate: the same grid runs Harvey forward or inverse
 // butterflies on register-resident data (no memory traffic), giving the
 // arithmetic ceiling of each Shoup-product variant of the butterfly code
@@ -91,6 +95,23 @@ __global__ void __launch_bounds__(256) butterfly_probe_kernel(uint32_t iters, ui
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc ^= (uint64_t)x[i];
     if (acc == 0x9e3779b97f4a7c15ull) sink[blockIdx.x] = acc;
+}
+
+// 16-byte grid-stride copy; src or dst may be pinned host memory (reached
+// over the CPU-GPU link through unified addressing).
+__global__ void __launch_bounds__(256) copy16_kernel(uint4* __restrict__ dst,
+                                                     const uint4* __restrict__ src, uint64_t n16) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n16; i += 4 * stride) {   // four loads in flight per thread
+        const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride],
+                    d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n16; i += stride) dst[i] = src[i];
 }
 
 typedef void (*BflyKernel)(uint32_t, uint64_t, uint64_t, uint64_t, uint64_t*);
@@ -181,5 +202,41 @@ extern "C" int hx_probe_butterfly_rate(uint32_t variant, uint32_t iters, uint64_
     if (t <= 0) return HX_ERR_CUDA;
     *butterflies_per_s = (double)blocks * 256.0 * iters * 4.0 / (t * 1e-3);
     if (ms) *ms = t;
+    return HX_OK;
+}
+
+extern "C" int hx_probe_copy_rate(void* dst, const void* src, uint64_t bytes, uint32_t iters,
+                                  uint32_t blocks_per_sm, double* bytes_per_s, float* ms,
+                                  hx_stream_t stream) {
+    if (!dst || !src || !bytes_per_s) return HX_ERR_NULL;
+    if (bytes == 0 || (bytes & 15) || ((uintptr_t)dst & 15) || ((uintptr_t)src & 15) ||
+        iters == 0 || blocks_per_sm == 0 || blocks_per_sm > 32)
+        return HX_ERR_ARG;
+    // only device memory or registered (pinned) host memory, through the
+    // device-side address the runtime reports for it
+    void* ends[2] = {dst, const_cast<void*>(src)};
+    for (auto& p : ends) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return HX_ERR_ARG;
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeHost &&
+            at.type != cudaMemoryTypeManaged)
+            return HX_ERR_ARG;
+        if (!at.devicePointer) return HX_ERR_ARG;
+        p = at.devicePointer;
+    }
+    const int blocks = sm_count() * (int)blocks_per_sm;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t n16 = bytes / 16;
+    uint4* d = (uint4*)ends[0];
+    const uint4* sr = (const uint4*)ends[1];
+    float t = time_probe(st, [&](uint32_t it) {
+        for (uint32_t k = 0; k < it; ++k) copy16_kernel<<<blocks, 256, 0, st>>>(d, sr, n16);
+    }, iters);
+    if (t <= 0) return HX_ERR_CUDA;
+    *bytes_per_s = (double)bytes * iters / (t * 1e-3);
+    if (ms) *ms = t / iters;
     return HX_OK;
 }
