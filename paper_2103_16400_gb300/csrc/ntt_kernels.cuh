@@ -155,10 +155,12 @@ struct TileCtx {
     uint32_t np_valid = 1;      // polynomials of this block's group that exist
 };
 
-// Global index of local tile element l = (bl, e, cl).
-template <int K>
+// Global index of local tile element l = (bl, e, cl).  Row passes (ROW: the
+// pass ends at the last stage, w = 0) hold whole rows, so their tile is the
+// contiguous range from b_base << K.
+template <int K, bool ROW = false>
 __device__ __forceinline__ uint64_t tile_gidx(uint32_t l, const TileCtx& t) {
-    if (t.w == 0) return (t.b_base << K) + l;
+    if (ROW || t.w == 0) return (t.b_base << K) + l;
     const uint32_t cl = l & ((1u << t.logGc) - 1);
     const uint32_t rho = l >> t.logGc;
     const uint64_t e = rho & ((1u << K) - 1);
@@ -188,7 +190,7 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
     constexpr int ELO = K - P - R;
     const uint32_t TEP = padded(c.nthreads << LOG_R);
     Wd xs[NP][RN];
-    uint64_t pfx[U];
+    uint32_t hp[U];   // 2^(s0+P) + the group's prefix: sub-stage k's twiddles start at hp << k
     uint32_t lbase[U], hiu[U];
     const uint32_t cmask = (1u << c.logGc) - 1;
 #pragma unroll
@@ -201,11 +203,11 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         const uint32_t ehi = t2 & ((1u << P) - 1);
         const uint32_t bl = t2 >> P;
         lbase[u] = (bl << (K + c.logGc)) | (ehi << (K - P + c.logGc)) | (elo << c.logGc) | cl;
-        pfx[u] = ((c.b_base + bl) << P) | ehi;
+        hp[u] = (1u << (c.s0 + P)) | (((uint32_t)c.b_base + bl) << P) | ehi;
         hiu[u] = (bl << P) | ehi;
     }
     const int sshift = ROW ? ELO : ELO + c.logGc;   // v stride in the tile
-    const int gshift = ELO + c.w;                   // v stride in global memory
+    const int gshift = ROW ? ELO : ELO + c.w;       // v stride in global memory
     uint32_t pl[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) pl[u] = pad(lbase[u]);
@@ -221,7 +223,7 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         if (SRC == IO_GLOBAL) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint64_t* p = c.gin + pp * c.poly_stride + tile_gidx<K>(lbase[u], c);
+                const uint64_t* p = c.gin + pp * c.poly_stride + tile_gidx<K, ROW>(lbase[u], c);
 #pragma unroll
                 for (int v = 0; v < (1 << R); ++v)
                     x[(v << (LOG_R - R)) | u] = (Wd)__ldg(p + ((uint64_t)v << gshift));
@@ -266,8 +268,7 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         const ulonglong2* tb[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            tb[u] = TWS ? tw + ((((1u << (P + k)) - 1) << c.logGb) + hiu[u])
-                        : tw + ((1ull << s) + (pfx[u] << k));
+            tb[u] = TWS ? tw + ((((1u << (P + k)) - 1) << c.logGb) + hiu[u]) : tw + (hp[u] << k);
 #pragma unroll
         for (int reg0 = 0; reg0 < RN; ++reg0) {
             if (reg0 & (1 << hb)) continue;
@@ -301,7 +302,7 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         if (DST == IO_GLOBAL) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                uint64_t* p = c.gout + pp * c.poly_stride + tile_gidx<K>(lbase[u], c);
+                uint64_t* p = c.gout + pp * c.poly_stride + tile_gidx<K, ROW>(lbase[u], c);
 #pragma unroll
                 for (int v = 0; v < (1 << R); ++v)
                     p[(uint64_t)v << gshift] = (uint64_t)x[(v << (LOG_R - R)) | u];
@@ -318,29 +319,40 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
 }
 
 // Cooperative coalesced copies of the whole tile (of each of the block's NP
-// polynomials) between HBM and shared memory.
-template <int K, int NP = 1>
+// polynomials) between HBM and shared memory.  Only row passes stage their
+// tiles, so the tile is the contiguous range from b_base << K.  Each thread
+// moves 2^(LOG_R-1) pairs; the loop count is a compile-time constant so that
+// all of a thread's loads are in flight before the first store.
+template <int K, int LOG_R, int NP = 1>
 __device__ __forceinline__ void tile_to_smem(uint64_t* sm, const TileCtx& c, uint32_t TE) {
+    constexpr int IT = 1 << (LOG_R - 1);
     for (uint32_t pp = 0; pp < (NP > 1 ? c.np_valid : 1u); ++pp) {
-        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(c.gin + pp * c.poly_stride);
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(
+            c.gin + pp * c.poly_stride + (c.b_base << K));
         uint64_t* smp = sm + pp * padded(TE);
-        for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
-            const uint32_t l = 2 * i;
-            const ulonglong2 v = __ldg(src + (tile_gidx<K>(l, c) >> 1));
-            smp[pad(l)] = v.x;        // l even: l and l + 1 share one 16-word row
-            smp[pad(l) + 1] = v.y;
+        ulonglong2 v[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) v[it] = __ldg(src + threadIdx.x + it * c.nthreads);
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const uint32_t l = 2 * (threadIdx.x + it * c.nthreads);
+            smp[pad(l)] = v[it].x;        // l even: l and l + 1 share one 16-word row
+            smp[pad(l) + 1] = v[it].y;
         }
     }
 }
 
-template <int K, int NP = 1>
+template <int K, int LOG_R, int NP = 1>
 __device__ __forceinline__ void smem_to_tile(const uint64_t* sm, const TileCtx& c, uint32_t TE) {
+    constexpr int IT = 1 << (LOG_R - 1);
     for (uint32_t pp = 0; pp < (NP > 1 ? c.np_valid : 1u); ++pp) {
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(c.gout + pp * c.poly_stride);
+        ulonglong2* dst =
+            reinterpret_cast<ulonglong2*>(c.gout + pp * c.poly_stride + (c.b_base << K));
         const uint64_t* smp = sm + pp * padded(TE);
-        for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
-            const uint32_t l = 2 * i;
-            dst[tile_gidx<K>(l, c) >> 1] = make_ulonglong2(smp[pad(l)], smp[pad(l) + 1]);
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const uint32_t i = threadIdx.x + it * c.nthreads, l = 2 * i;
+            dst[i] = make_ulonglong2(smp[pad(l)], smp[pad(l) + 1]);
         }
     }
 }
@@ -423,7 +435,7 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
         tw = tws;
     }
     if (staged_in) {
-        tile_to_smem<K, NP>(sm, c, TE);
+        tile_to_smem<K, LOG_R, NP>(sm, c, TE);
         if constexpr (TWS) cp_async_wait<0>();
         __syncthreads();
     }
@@ -435,7 +447,7 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
         ntt_rounds<FWD, COLUMN, uint64_t, 0, LOG_R, K, 0, NP, TWS>(sm, tw, lc, c);
     if (staged_out) {
         __syncthreads();
-        smem_to_tile<K, NP>(sm, c, TE);
+        smem_to_tile<K, LOG_R, NP>(sm, c, TE);
     }
 }
 
@@ -559,7 +571,7 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
     constexpr int U = 1 << (LOG_R - R);
     constexpr int ELO = K - P - R;
     Wd x[RN];
-    uint64_t pfx[U];
+    uint32_t hp[U];
     uint32_t lbase[U];
     const uint32_t cmask = (1u << c.logGc) - 1;
 #pragma unroll
@@ -572,7 +584,7 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
         const uint32_t ehi = t2 & ((1u << P) - 1);
         const uint32_t bl = t2 >> P;
         lbase[u] = (bl << (K + c.logGc)) | (ehi << (K - P + c.logGc)) | (elo << c.logGc) | cl;
-        pfx[u] = ((c.b_base + bl) << P) | ehi;
+        hp[u] = (1u << (c.s0 + P)) | (((uint32_t)c.b_base + bl) << P) | ehi;
     }
     const int sshift = ELO + c.logGc;
 #pragma unroll
@@ -601,7 +613,7 @@ __device__ __forceinline__ void pipe_round(uint64_t* sm, const ulonglong2* __res
         }
         const ulonglong2* tb[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) tb[u] = tw + ((1ull << (c.s0 + P + k)) + (pfx[u] << k));
+        for (int u = 0; u < U; ++u) tb[u] = tw + (hp[u] << k);
 #pragma unroll
         for (int reg0 = 0; reg0 < RN; ++reg0) {
             if (reg0 & (1 << hb)) continue;

@@ -67,7 +67,12 @@ __global__ void __launch_bounds__(512) ntt_tensor_inv_kernel(PassArgs a, TensorI
     const ulonglong2* E = reinterpret_cast<const ulonglong2*>(t.E + base);
     const ulonglong2 zero = make_ulonglong2(0, 0);
     const uint32_t TEP = padded(TE);
-    for (uint32_t i = threadIdx.x; i < TE / 2; i += c.nthreads) {
+    // 2^(LOG_R-1) pairs a thread; a compile-time count lets the loads of
+    // consecutive steps overlap (one step at a time for three outputs, whose
+    // registers are already full)
+#pragma unroll(NPF == 3 ? 1 : 4)
+    for (int it = 0; it < (1 << (LOG_R - 1)); ++it) {
+        const uint32_t i = threadIdx.x + it * c.nthreads;
         const uint32_t l = 2 * i;
         const bool need0 = NPF == 3 || k != 2, need1 = NPF == 3 || k != 0;
         const ulonglong2 x0 = need0 ? __ldg(A0 + i) : zero;
