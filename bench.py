@@ -86,11 +86,15 @@ def slots_per_butterfly(q):
 
 
 #: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, both pass launches)
-#: of one forward call over 4 polynomials x 32 mixed limbs at N = 65536, from one
-#: ncu --set full capture of that call under the schedule below; reported only
-#: when the tuned forward schedule is that one (other kernels, other traffic).
-FWD_TRAFFIC_BYTES = 67246848 + 16910592 + 100663296 + 17612544
-FWD_TRAFFIC_SCHEDULE = [[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]
+#: of one forward call over 4 polynomials x 32 mixed limbs at N = 65536, from
+#: ncu --set full captures of that call under each schedule listed; reported
+#: only when the tuned forward schedule is one of them (other kernels, other
+#: traffic).  Keyed by the schedule's JSON.
+FWD_TRAFFIC_BYTES = {
+    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]": 67250688 + 19209472 + 100657664 + 17378304,
+    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]": 67314432 + 22614784 + 100587520 + 16981760,
+    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]": 67316480 + 23170816 + 100593152 + 17588480,
+}
 
 
 def imad_slots_per_transform(N, moduli):
@@ -490,7 +494,11 @@ def run_case(args):
     xs = [to_device(W.poly_batch(wl.seed + k, 0, P, wl.moduli, N)) for k in range(n_sets)]
     ys = [empty(x.shape) for x in xs]
     plan = capi.Plan(N, wl.moduli)
-    if args.tuned and args.case in ("fwd", "inv"):
+    if args.schedule and args.case in ("fwd", "inv"):
+        sched = [tuple(p) for p in json.loads(args.schedule)]
+        plan.set_schedule(sched, plan.FORWARD if args.case == "fwd" else plan.INVERSE)
+        out["schedule"] = [list(p) for p in sched]
+    elif args.tuned and args.case in ("fwd", "inv"):
         from paper_2103_16400_gb300 import tune as hx_tune
         t = hx_tune.tune(plan, P, direction=plan.FORWARD if args.case == "fwd" else plan.INVERSE,
                          verbose=bool(os.environ.get("HX_TUNE_VERBOSE")))
@@ -595,6 +603,8 @@ def main():
     ap.add_argument("--polys", type=int, default=8, help="polynomials per call for --case fwd/inv")
     ap.add_argument("--tuned", action="store_true",
                     help="--case fwd/inv: apply the autotuned schedule (cached) instead of the default")
+    ap.add_argument("--schedule", default=None,
+                    help="--case fwd/inv: JSON list of passes to apply instead (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -653,7 +663,7 @@ def main():
     achieved = alg_slots / (fwd_call_ms * 1e-3)
     fwd_bytes = 4 * 16 * N * nl
     fwd_sched = getattr(step, "tuned", {}).get("forward", {}).get("forward")
-    traffic = (FWD_TRAFFIC_BYTES if (N, nl) == (1 << 16, 32) and fwd_sched == FWD_TRAFFIC_SCHEDULE
+    traffic = (FWD_TRAFFIC_BYTES.get(json.dumps(fwd_sched)) if (N, nl) == (1 << 16, 32)
                else None)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": imad_rate / 1e12,
                 "unit": "T IMAD-slot/s", "frac": achieved / imad_rate, "traffic": traffic,

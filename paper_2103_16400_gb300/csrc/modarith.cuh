@@ -4,7 +4,8 @@
 //
 // Two widths, chosen per modulus (the paper's BitShift idea, Section 3.2):
 //   * wide  : q < 2^62, words of beta = 2^64; a Shoup product needs the high
-//             word of a 64x64 product plus two low words.
+//             word of a 64x64 product plus two low words.  Below 2^61 the high
+//             word is truncated to three partial products (lazy bound 4q).
 //   * narrow: q < 2^30, words of beta = 2^32; the Shoup product is three 32-bit
 //             multiplies (one high half, two low halves).
 // The Harvey butterflies (Section 2.2) need q < beta/4 in both cases.

@@ -2,9 +2,10 @@
 // ntt_fwd.cu and ntt_inv.cu).
 //
 // The forward transform is the radix-2 Cooley-Tukey NTT of Section 2.2 with
-// the Harvey butterfly (values kept lazily in [0, 4q)); the inverse is the
+// the Harvey butterfly (values kept lazily in [0, 2m)); the inverse is the
 // radix-2 Gentleman-Sande InvNTT with the Harvey inverse butterfly (values in
-// [0, 2q)) and the N^-1 scaling folded into its last stage.  Both index the
+// [0, m)) and the N^-1 scaling folded into its last stage, m = 2q with the
+// exact Shoup quotient, 4q with the truncated one (Word below).  Both index the
 // twiddles as the paper's algorithms do: stage s (s = 0 .. log2 N - 1,
 // m = 2^s) pairs element j with j + N/2^(s+1) and uses table entry
 // 2^s + (j >> (log2 N - s)) -- psi_rev for the forward, psi^-1_rev for the
@@ -21,7 +22,9 @@
 // (column passes, and the low-stage end of row passes); otherwise the tile is
 // staged through shared memory with 16-byte vector copies.  Twiddle pairs
 // {W, W'} are read through the read-only path from one base pointer per
-// (round, sub-stage, group) plus compile-time offsets.
+// (round, sub-stage, group) plus compile-time offsets, or from a copy of the
+// tile's pairs staged in shared memory.  A persistent double-buffered
+// variant streams tiles with cp.async.
 #pragma once
 #include <stdint.h>
 
