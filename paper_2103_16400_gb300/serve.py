@@ -7,19 +7,22 @@ EltwiseMultMod with input_mod_factor 4, inverse NTT to [0, q).
 
 The paper's polynomial layer is single-threaded and per call (Section 3);
 its integration section notes that one call is too small to offload to an
-accelerator (Section 4).  The server answers that by batching: an engine
-thread repeatedly
-  1. moves newly submitted requests to a FIFO wait list,
-  2. admits waiting requests in order while their device memory (operands,
-     one result per request, in HBM) fits the HBM budget and a stream slot
-     is free -- requests that arrive while earlier batches are still on the
-     GPU join the next batch (continuous batching),
-  3. launches the admitted batch on its own CUDA stream as one ragged
-     product call (hx_polymul_ragged: five kernels for the whole batch,
-     whatever its mix of N and moduli) into a workspace taken from the
-     torch allocator, with one upload and one download for host operands,
-  4. completes the requests of every batch whose end event has fired,
-     stamping their latency, and releases their budget.
+accelerator (Section 4).  The server answers that by batching, with two
+threads and no polling:
+  * the engine thread sleeps on the request queue; woken by a submission
+    (or by a finished batch), it moves every newly submitted request to a
+    FIFO wait list and admits waiting requests in order while their device
+    memory (operands, one result per request, in HBM) fits the HBM budget
+    and a stream slot is free -- requests that arrive while earlier batches
+    are still on the GPU join the next batch (continuous batching) -- and
+    launches each admitted batch on its own CUDA stream as one ragged
+    product call (hx_polymul_ragged: five kernels for the whole batch,
+    whatever its mix of N and moduli) into a workspace taken from the torch
+    allocator, with one upload and one download for host operands;
+  * the completer thread waits on each launched batch's end event in turn
+    (the wait releases the interpreter lock), completes its requests,
+    stamping their latency, returns their budget and stream, and wakes the
+    engine for any requests that were waiting for them.
 Batches on different streams overlap on the GPU.  Plans (and so the twiddle
 tables) are created once per (N, moduli) and stay resident.
 
@@ -80,9 +83,12 @@ class BudgetError(ValueError):
     pass
 
 
+_WAKE = object()   # queue token: re-check admission, nothing submitted
+
+
 class Server:
-    """Engine thread + streams; `submit()` is thread-safe and returns a
-    Future that resolves to the product (uint64 [limbs][N])."""
+    """Engine and completer threads + streams; `submit()` is thread-safe and
+    returns a Future that resolves to the product (uint64 [limbs][N])."""
 
     def __init__(self, hbm_budget: int = 64 << 30, streams: int = 3,
                  max_batch: int = 256, device: int = 0):
@@ -96,13 +102,15 @@ class Server:
         self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
         self.free_streams = list(range(streams))
         self.in_use = 0
+        self.n_inflight = 0
         self.plans: Dict[Tuple[int, Tuple[int, ...]], capi.Plan] = {}
-        self.inbox: "queue.Queue[Request]" = queue.Queue()
+        self.inbox: "queue.Queue" = queue.Queue()
+        self.done_q: "queue.Queue" = queue.Queue()
         self.waiting: "collections.deque[Request]" = collections.deque()
-        self.inflight: List[dict] = []
         self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "launches": 0}
+        self._lock = threading.Lock()            # in_use, free_streams, n_inflight, stats
         self._stop = threading.Event()
-        self._thread: Optional[threading.Thread] = None
+        self._threads: List[threading.Thread] = []
         self._error: Optional[BaseException] = None
 
     # ------------------------------------------------------------ client side
@@ -121,17 +129,26 @@ class Server:
         return req.future
 
     def start(self) -> "Server":
-        self._thread = threading.Thread(target=self._run, name="hexgpu-serve", daemon=True)
-        self._thread.start()
+        self._threads = [threading.Thread(target=self._run, name="hexgpu-serve", daemon=True),
+                         threading.Thread(target=self._complete, name="hexgpu-complete",
+                                          daemon=True)]
+        for t in self._threads:
+            t.start()
         return self
 
     def stop(self, drain: bool = True):
         if drain:
-            while (not self.inbox.empty() or self.waiting or self.inflight) and self._error is None:
+            while self._error is None:
+                with self._lock:
+                    busy = self.n_inflight > 0
+                if not (busy or self.waiting or not self.inbox.empty()):
+                    break
                 time.sleep(0.0005)
         self._stop.set()
-        if self._thread:
-            self._thread.join()
+        self.inbox.put(_WAKE)
+        self.done_q.put(None)
+        for t in self._threads:
+            t.join()
         if self._error is not None:
             raise self._error
 
@@ -142,48 +159,56 @@ class Server:
         self.stop(drain=exc[0] is None)
 
     # ------------------------------------------------------------ engine
+    def _fail(self, e: BaseException):
+        self._error = e
+        for r in list(self.waiting):
+            if not r.future.done():
+                r.future.set_exception(e)
+
     def _run(self):
-        torch = self.torch
-        torch.cuda.set_device(self.device)
+        self.torch.cuda.set_device(self.device)
         try:
             while not self._stop.is_set():
-                moved = self._drain_inbox()
-                self._complete_finished()
-                launched = self._admit_and_launch()
-                if not (moved or launched):
-                    time.sleep(0.0001)
+                try:
+                    item = self.inbox.get(timeout=0.05)
+                except queue.Empty:
+                    continue
+                if item is not _WAKE:
+                    self.waiting.append(item)
+                self._drain_inbox()
+                while self._admit_and_launch():
+                    self._drain_inbox()
         except BaseException as e:              # surface engine errors to the client
-            self._error = e
-            for r in list(self.waiting):
-                r.future.set_exception(e)
-            for b in self.inflight:
-                for r in b["reqs"]:
-                    r.future.set_exception(e)
+            self._fail(e)
 
-    def _drain_inbox(self) -> bool:
-        moved = False
+    def _drain_inbox(self):
         while True:
             try:
-                self.waiting.append(self.inbox.get_nowait())
-                moved = True
+                item = self.inbox.get_nowait()
             except queue.Empty:
-                return moved
+                return
+            if item is not _WAKE:
+                self.waiting.append(item)
 
     def _admit_and_launch(self) -> bool:
-        if not self.waiting or not self.free_streams:
+        if not self.waiting:
             return False
-        batch, need = [], 0
-        while self.waiting and len(batch) < self.max_batch:
-            r = self.waiting[0]
-            if self.in_use + need + r.device_bytes > self.budget:
-                break
-            batch.append(self.waiting.popleft())
-            need += r.device_bytes
-        if not batch:
-            return False
-        self.in_use += need
-        sid = self.free_streams.pop()
-        self.inflight.append(self._launch(batch, sid, need))
+        with self._lock:
+            if not self.free_streams:
+                return False
+            batch, need = [], 0
+            while self.waiting and len(batch) < self.max_batch:
+                r = self.waiting[0]
+                if self.in_use + need + r.device_bytes > self.budget:
+                    break
+                batch.append(self.waiting.popleft())
+                need += r.device_bytes
+            if not batch:
+                return False
+            self.in_use += need
+            self.n_inflight += 1
+            sid = self.free_streams.pop()
+        self.done_q.put(self._launch(batch, sid, need))
         return True
 
     def _launch(self, reqs: List[Request], sid: int, need: int) -> dict:
@@ -229,33 +254,44 @@ class Server:
                 out_host.copy_(res, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
-        self.stats["batches"] += 1
-        self.stats["requests"] += len(reqs)
-        self.stats["launches"] += 5
-        self.stats["max_batch"] = max(self.stats["max_batch"], len(reqs))
+        with self._lock:
+            self.stats["batches"] += 1
+            self.stats["requests"] += len(reqs)
+            self.stats["launches"] += 5
+            self.stats["max_batch"] = max(self.stats["max_batch"], len(reqs))
         work = (res, res_off, out_host, staged, pinned, ws)
         return {"reqs": reqs, "work": work, "event": ev, "sid": sid, "bytes": need}
 
-    def _complete_finished(self):
-        still = []
-        for b in self.inflight:
-            if not b["event"].query():
-                still.append(b)
-                continue
-            now = time.perf_counter()
-            res, res_off, out_host, _, _, _ = b["work"]
-            hv = out_host.numpy().view(np.uint64) if out_host is not None else None
-            for k, r in enumerate(b["reqs"]):
-                lo, hi = int(res_off[k]), int(res_off[k + 1])
-                if r.resident:
-                    r.result = res[lo:hi].view(r.limbs, r.N)
-                else:
-                    r.result = hv[lo:hi].reshape(r.limbs, r.N).copy()
-                r.done = now
-                r.future.set_result(r.result)
-            self.in_use -= b["bytes"]
-            self.free_streams.append(b["sid"])
-        self.inflight = still
+    # ------------------------------------------------------------ completer
+    def _complete(self):
+        self.torch.cuda.set_device(self.device)
+        while True:
+            b = self.done_q.get()
+            if b is None:
+                return
+            try:
+                b["event"].synchronize()
+                now = time.perf_counter()
+                res, res_off, out_host, _, _, _ = b["work"]
+                hv = out_host.numpy().view(np.uint64) if out_host is not None else None
+                for k, r in enumerate(b["reqs"]):
+                    lo, hi = int(res_off[k]), int(res_off[k + 1])
+                    if r.resident:
+                        r.result = res[lo:hi].view(r.limbs, r.N)
+                    else:
+                        r.result = hv[lo:hi].reshape(r.limbs, r.N).copy()
+                    r.done = now
+                    r.future.set_result(r.result)
+            except BaseException as e:
+                self._error = e
+                for r in b["reqs"]:
+                    if not r.future.done():
+                        r.future.set_exception(e)
+            with self._lock:
+                self.in_use -= b["bytes"]
+                self.free_streams.append(b["sid"])
+                self.n_inflight -= 1
+            self.inbox.put(_WAKE)
 
 
 def serve_one_by_one(reqs: Sequence[Request], arrivals: Optional[Sequence[float]] = None,
