@@ -459,12 +459,13 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
 // loads needs): 72 with 16 elements a thread (it would take up to 102:
 // forward call 104 -> 92 us under the schedule with a 7-stage column pass),
 // 48 with 8 (inverse call 80 -> 74 us), 96 with two polynomials a thread
-// (spills stay within 16 bytes).
+// (spills stay within 16 bytes).  Blocks have at most 512 threads, which
+// 512 x 96 registers fit.
 #define HX_PASS_MAXNREG __maxnreg__(LOG_R == 4 ? 72 : NP > 1 ? 96 : 48)
 
 // One block per (tile, group of NP polynomials, limb).
 template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false>
-__global__ void __launch_bounds__(512) HX_PASS_MAXNREG ntt_pass_kernel(PassArgs a) {
+__global__ void HX_PASS_MAXNREG ntt_pass_kernel(PassArgs a) {
     extern __shared__ uint64_t sm[];
     const uint32_t limb = blockIdx.y;
     const uint32_t n_groups = (a.n_polys + NP - 1) / NP;
