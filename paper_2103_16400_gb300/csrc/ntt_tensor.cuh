@@ -18,8 +18,14 @@ namespace hx {
 // NPF = 1: one block per (tile, output k, ciphertext, limb); NPF = 3: one
 // block per (tile, ciphertext, limb) computing all three r_k from one read of
 // the operands and transforming them with shared twiddle loads.
+// Register caps (measured on GB300 at N = 2^16 x 32 limbs): 96 for three
+// outputs a block -- five blocks of 128 threads per SM instead of four; the
+// tensor + inverse call 108.5 -> 103.0 us -- and as the per-tile passes for
+// one output a block.  Blocks have at most 512 threads, which 512 x 96
+// registers fit.
 template <int LOG_R, int K, bool TWS, int NPF>
-__global__ void __launch_bounds__(512) ntt_tensor_inv_kernel(PassArgs a, TensorIn t) {
+__global__ void __maxnreg__(NPF == 3 ? 96 : (LOG_R == 4 ? 72 : 64))
+    ntt_tensor_inv_kernel(PassArgs a, TensorIn t) {
     extern __shared__ uint64_t sm[];
     const uint32_t li = blockIdx.y, limb = t.limb0 + li;
     const uint32_t G = (NPF == 3 ? 1 : 3) * t.n_ct;
