@@ -454,14 +454,15 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
     }
 }
 
-// Register caps of the per-tile kernels, chosen by measurement on GB300 (the
-// compiler's own choice leaves fewer blocks resident than the latency of the
-// loads needs): 72 with 16 elements a thread (it would take up to 102:
-// forward call 104 -> 92 us under the schedule with a 7-stage column pass),
-// 48 with 8 (inverse call 80 -> 74 us), 96 with two polynomials a thread
-// (spills stay within 16 bytes).  Blocks have at most 512 threads, which
-// 512 x 96 registers fit.
-#define HX_PASS_MAXNREG __maxnreg__(LOG_R == 4 ? 72 : NP > 1 ? 96 : 48)
+// Register caps of the per-tile kernels, chosen by measurement on GB300 at
+// N = 2^16 x 32 limbs (the compiler's own choice leaves fewer blocks resident
+// than the latency of the loads needs): 72 with 16 elements a thread (it
+// would take up to 102: forward call 104 -> 92 us under the schedule with a
+// 7-stage column pass); with 8, 40 in the forward (92 -> 90 us) and 48 in
+// the inverse (80 -> 74 us); 96 with two polynomials a thread (spills stay
+// within 16 bytes).  Blocks have at most 512 threads, which 512 x 96
+// registers fit.
+#define HX_PASS_MAXNREG __maxnreg__(LOG_R == 4 ? 72 : NP > 1 ? 96 : FWD ? 40 : 48)
 
 // One block per (tile, group of NP polynomials, limb).
 template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false>
