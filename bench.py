@@ -91,9 +91,9 @@ def slots_per_butterfly(q):
 #: only when the tuned forward schedule is one of them (other kernels, other
 #: traffic).  Keyed by the schedule's JSON.
 FWD_TRAFFIC_BYTES = {
-    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]": 67250688 + 19209472 + 100657664 + 17378304,
-    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]": 67314432 + 22614784 + 100587520 + 16981760,
-    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]": 67316480 + 23170816 + 100593152 + 17588480,
+    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]": 67256320 + 17201152 + 100655616 + 17272064,
+    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]": 67316992 + 22987008 + 100586752 + 17123840,
+    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]": 67325952 + 22792448 + 100587008 + 17210880,
 }
 
 
