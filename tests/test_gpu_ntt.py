@@ -121,13 +121,14 @@ def _largest_ntt_prime_below(bound, two_n):
 def test_truncated_quotient_boundary(hexlib):
     """64-bit limbs with q < 2^61 take the truncated-quotient Shoup product
     (lazy bound 4q), q >= 2^61 the exact one (2q): the largest NTT prime below
-    2^61 and the smallest above, with every coefficient at the top of the
-    allowed input range and with random inputs, forward and inverse, canonical
-    and lazy outputs."""
+    2^61 and the smallest above (and likewise around 2^60 and 2^50), with
+    every coefficient at the top of the allowed input range and with random
+    inputs, forward and inverse, canonical and lazy outputs."""
     N = 1 << 13
     qs = [_largest_ntt_prime_below(1 << 61, 2 * N), W.ntt_primes(62, 2 * N, 1)[0],
+          _largest_ntt_prime_below(1 << 60, 2 * N), W.ntt_primes(61, 2 * N, 1)[0],
           _largest_ntt_prime_below(1 << 50, 2 * N), MIXED3[2]]
-    assert qs[0] < (1 << 61) <= qs[1]
+    assert qs[0] < (1 << 61) <= qs[1] and qs[2] < (1 << 60) <= qs[3]
     plan = Plan(N, qs)
     top = np.stack([np.full(N, 4 * q - 1, dtype=np.uint64) for q in qs])[None]
     rnd = W.poly_batch(W.SEED_BASE + 520, 1, 3, qs, N)
