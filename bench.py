@@ -125,6 +125,7 @@ class HexStep:
         self.R = empty((3, L, N))
         self.stream = torch.cuda.current_stream()
         self.fwd_events = []
+        self.inv_events = []
 
     def run(self, i, record=False):
         c, N, st = self.capi, self.N, self.stream
@@ -142,6 +143,10 @@ class HexStep:
         # inverse's first pass (operands back to back)
         c.hx_tensor_fma_inverse(self.plan, R[0], R[1], R[2], A[0], A[1], A[2], A[3], self.s,
                                 es[0], es[1], es[2], 1, 4, st)
+        if record:
+            e2 = self.torch.cuda.Event(enable_timing=True)
+            e2.record(st)
+            self.inv_events.append((e1, e2))
         return [R[0:1], R[1:2], R[2:3]]
 
 
@@ -649,6 +654,7 @@ def main():
     launches = capi.hx_launch_count() - launches0
     total_ms = t0.elapsed_time(t1)
     fwd_ms = [a.elapsed_time(b) for a, b in step.fwd_events]
+    inv_ms = [a.elapsed_time(b) for a, b in step.inv_events]
     total_ms = shard.max_over_ranks(total_ms, device="cuda")
     barrier()
 
@@ -673,6 +679,7 @@ def main():
                 "fwd_call_us": fwd_call_ms * 1e3,
                 "alg_slots_per_call": alg_slots,
                 "hbm_gbs_algorithmic": fwd_bytes / (fwd_call_ms * 1e-3) / 1e9,
+                "dram_gbs_measured": (traffic / (fwd_call_ms * 1e-3) / 1e9) if traffic else None,
                 "peak_source": "hx_probe_int_mul_rate mad.lo.u32 (1 slot), measured live",
                 "schedules": {k: v.get("forward" if k == "forward" else "inverse")
                               for k, v in getattr(step, "tuned", {}).items()}}
@@ -721,6 +728,12 @@ def main():
                     "ms_per_step": e2e_ms / e2e_steps,
                     "how": "pinned host -> device -> pinned host every step; upload, "
                            "compute and download on three streams, two buffer sets"},
+            "calls": {"forward_us": fwd_call_ms * 1e3,
+                      "forward_limb_transforms_per_s": 4 * nl / (fwd_call_ms * 1e-3),
+                      "tensor_inverse_us": float(np.mean(inv_ms)) * 1e3,
+                      "tensor_inverse_limb_transforms_per_s":
+                          3 * nl / (float(np.mean(inv_ms)) * 1e-3),
+                      "how": "CUDA events around each call inside the timed region"},
             "gpu_launches": launches,
             "clocks": clocks.summary()}
     # the batched and serving reports run on rank 0 only; the other ranks wait
