@@ -209,6 +209,60 @@ def ragged_report(torch, n_polys=512, reps=5):
             "speedup_vs_per_limb": t_limb / t_batch, "bit_exact_equal": bool(same)}
 
 
+# ------------------------------------------------------------------ element-wise
+def hbm_peak_gbs():
+    """Measured copy bandwidth (read + write bytes) of this machine's GPUs, from
+    the peaks file at the repository root, else the profiling fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def eltwise_report(torch, N=1 << 16, nl=32, P=4, reps=20):
+    """The element-wise kernels on 4 polynomials x 32 limbs x 65536 (64 MiB
+    an operand; two rotating operand sets exceed L2): algorithmic HBM bytes
+    (8 B per operand element read or written) per second against the
+    measured copy bandwidth."""
+    from paper_2103_16400_gb300 import capi
+    from paper_2103_16400_gb300.tensors import empty, to_device
+    wl = W.ciphertext_tensor(N=N, n_limbs=nl)
+    mods = wl.moduli
+    sets = [(to_device(W.poly_batch(wl.seed + 40 + k, 0, P, mods, N)),
+             to_device(W.poly_batch(wl.seed + 40 + k, 1, P, mods, N)),
+             to_device(W.poly_batch(wl.seed + 40 + k, 2, P, mods, N))) for k in range(2)]
+    outs = [empty((P, nl, N)) for _ in range(2)]
+    s = W.scalars(wl.seed, 21, mods)
+    st = torch.cuda.current_stream()
+    peak, src = hbm_peak_gbs()
+    ops = {
+        "add": (3, lambda a, b, d, r: capi.hx_eltwise_add_mod(r, a, b, N, mods, P, st)),
+        "sub": (3, lambda a, b, d, r: capi.hx_eltwise_sub_mod(r, a, b, N, mods, P, st)),
+        "negate": (2, lambda a, b, d, r: capi.hx_eltwise_negate_mod(r, a, N, mods, P, st)),
+        "mult": (3, lambda a, b, d, r: capi.hx_eltwise_mult_mod(r, a, b, N, mods, P, 1, st)),
+        "fma": (3, lambda a, b, d, r: capi.hx_eltwise_fma_mod(r, a, s, d, N, mods, P, 1, st)),
+        "fma_no_addend": (2, lambda a, b, d, r: capi.hx_eltwise_fma_mod(r, a, s, None, N, mods,
+                                                                        P, 1, st)),
+    }
+    out = {"workload": f"{P} polys x {nl} limbs x {N}, mixed 30/50/60-bit",
+           "peak_gbs": peak, "peak_source": f"{src} copy bandwidth (read + write bytes)"}
+    for name, (operands, fn) in ops.items():
+        for k in range(2):
+            fn(*sets[k], outs[k])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(reps):
+            fn(*sets[i % 2], outs[i % 2])
+        e1.record(st)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        gbs = operands * 8 * P * nl * N / (us * 1e-6) / 1e9
+        out[name] = {"us": us, "alg_gbs": gbs, "frac": gbs / peak}
+    return out
+
+
 # ------------------------------------------------------------------ serving
 def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30):
     """Poisson arrivals of polynomial-multiply requests (N uniform over
@@ -737,6 +791,8 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks.summary()}
     # the batched and serving reports run on rank 0 only; the other ranks wait
+    if rank == 0:
+        line["eltwise"] = eltwise_report(torch)
     if rank == 0 and not args.no_ragged:
         line["batched"] = ragged_report(torch)
     if rank == 0 and not args.no_serving:
