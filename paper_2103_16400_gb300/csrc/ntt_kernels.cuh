@@ -680,7 +680,7 @@ __device__ __forceinline__ void pipe_rounds(uint64_t* sm, const ulonglong2* __re
 }
 
 template <bool FWD, bool COLUMN, int LOG_R, int K>
-__global__ void __launch_bounds__(256, LOG_R == 3 ? 4 : 2) ntt_pipe_kernel(PassArgs a) {
+__global__ void __maxnreg__(LOG_R == 4 ? 72 : FWD ? 40 : 48) ntt_pipe_kernel(PassArgs a) {
     extern __shared__ uint64_t sm[];
     const int logTE = a.logGb + K + a.logGc;
     const uint32_t TE = 1u << logTE;
