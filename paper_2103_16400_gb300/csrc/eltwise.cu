@@ -76,8 +76,10 @@ __device__ __forceinline__ uint64_t elt_apply(uint64_t a, uint64_t b, const EltC
     }
 }
 
+// 32 registers: with 256-thread blocks eight fit on an SM, so the grid of
+// about eight blocks an SM (elt_grid) is resident in one wave.
 template <int OP, int INMF, bool ADDEND>
-__global__ void __launch_bounds__(256) eltwise_kernel(uint64_t* __restrict__ r,
+__global__ void __maxnreg__(32) eltwise_kernel(uint64_t* __restrict__ r,
                                                       const uint64_t* __restrict__ a,
                                                       const uint64_t* __restrict__ b,
                                                       EltConsts c, EltGeom g) {
