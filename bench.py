@@ -92,6 +92,7 @@ def slots_per_butterfly(q):
 #: traffic).  Keyed by the schedule's JSON.
 FWD_TRAFFIC_BYTES = {
     "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]": 67256320 + 17201152 + 100655616 + 17272064,
+    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 1]]": 67247872 + 16849920 + 100657664 + 17978624,
     "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]": 67316992 + 22987008 + 100586752 + 17123840,
     "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]": 67325952 + 22792448 + 100587008 + 17210880,
 }
