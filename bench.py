@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import gc
 import json
 import os
 import platform
@@ -265,7 +266,45 @@ def eltwise_report(torch, N=1 << 16, nl=32, P=4, reps=20):
 
 
 # ------------------------------------------------------------------ serving
-def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30):
+def cgroup_cpu():
+    """The container's CPU quota and throttling counters (cgroup v2, else v1),
+    or None: a quota that runs out stalls every thread of the process until
+    the next period, which shows in tail latency."""
+    for d in ("/sys/fs/cgroup", "/sys/fs/cgroup/cpu,cpuacct", "/sys/fs/cgroup/cpu"):
+        try:
+            with open(os.path.join(d, "cpu.stat")) as f:
+                st = dict(line.split() for line in f if len(line.split()) == 2)
+        except OSError:
+            continue
+        out = {"nr_throttled": int(st.get("nr_throttled", 0)),
+               "throttled_usec": int(st.get("throttled_usec", int(st.get("throttled_time", 0)) // 1000))}
+        try:
+            with open(os.path.join(d, "cpu.max")) as f:
+                quota, period = f.read().split()
+            out["quota_cpus"] = None if quota == "max" else int(quota) / int(period)
+        except (OSError, ValueError):
+            try:
+                with open(os.path.join(d, "cpu.cfs_quota_us")) as f:
+                    quota = int(f.read())
+                with open(os.path.join(d, "cpu.cfs_period_us")) as f:
+                    period = int(f.read())
+                out["quota_cpus"] = None if quota < 0 else quota / period
+            except (OSError, ValueError):
+                out["quota_cpus"] = None
+        return out
+    return None
+
+
+def _throttled_since(before):
+    now = cgroup_cpu()
+    if before is None or now is None:
+        return None
+    return {"periods": now["nr_throttled"] - before["nr_throttled"],
+            "usec": now["throttled_usec"] - before["throttled_usec"]}
+
+
+def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30,
+                   blocking_wait=True):
     """Poisson arrivals of polynomial-multiply requests (N uniform over
     {2^12, 2^14, 2^16}, 4-32 limbs of the mixed 30/50/60-bit basis, operands
     uniform mod q and resident in HBM) at each rate: the continuous-batching
@@ -289,43 +328,50 @@ def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30
         return [serve.Request(N, tuple(moduli[:L]), pool[N][k][0][:L], pool[N][k][1][:L])
                 for N, L, k in spec]
 
-    srv = serve.Server(hbm_budget=budget, streams=3)
+    streams = [torch.cuda.Stream() for _ in range(3)]   # shared by every server below
+    srv = serve.Server(hbm_budget=budget, streams=streams, blocking_wait=blocking_wait)
     for N in Ns:                                   # plans (twiddles) resident up front
         for L in range(4, 33):
             srv.plan(N, moduli[:L])
     plans = dict(srv.plans)
-    # warm both paths (torch allocator, pinned pools, kernels)
-    warm = requests()[:64]
+    # warm both paths (kernels, and the allocator's blocks on the servers'
+    # streams: every request at once, so batches reach their largest sizes)
     with srv:
-        for f in [srv.submit(r) for r in warm]:
+        for f in [srv.submit(r) for r in requests()]:
             f.result()
-    srv = serve.Server(hbm_budget=budget, streams=3)
-    srv.plans = plans
     serve.serve_one_by_one(requests()[:64], plans=plans)
     torch.cuda.synchronize()
+    gc.collect()
+    gc.freeze()        # the long-lived heap leaves the collector's scans
 
     lt_per_req = [3 * L for _, L, _ in spec]
     out = []
     for rate in rates:
         arrivals = np.cumsum(-np.log1p(-u) / rate)
         served = requests()
-        srv = serve.Server(hbm_budget=budget, streams=3)
+        srv = serve.Server(hbm_budget=budget, streams=streams, blocking_wait=blocking_wait)
         srv.plans = plans
+        cg = cgroup_cpu()
         srv.start()
         t0 = time.perf_counter()
         futs = []
         for r, t in zip(served, arrivals):
-            while True:                  # wait for the arrival without holding the GIL
-                wait = t - (time.perf_counter() - t0)
-                if wait <= 0:
-                    break
-                time.sleep(wait if wait > 2e-4 else 0)
-            futs.append(srv.submit(r))
+            # sleep until the arrival (the interpreter lock stays free for the
+            # server's threads); requests already due go in at once, each
+            # stamped with its scheduled arrival, so lateness here counts as
+            # latency, exactly as in the one-by-one baseline
+            wait = t - (time.perf_counter() - t0)
+            if wait > 1e-4:
+                time.sleep(wait - 5e-5)
+            futs.append(srv.submit(r, arrival=t0 + t))
         for f in futs:
             f.result(timeout=600)
         srv.stop()
+        thr_served = _throttled_since(cg)
         base = requests()
+        cg = cgroup_cpu()
         serve.serve_one_by_one(base, arrivals, plans=plans)
+        thr_base = _throttled_since(cg)
         same = all(torch.equal(a.result, b.result) for a, b in zip(served, base))
 
         def summary(rs):
@@ -337,10 +383,16 @@ def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30
                     "mean_ms": float(lat.mean())}
         out.append({"offered_rate_per_s": rate, "requests": n_req, "served": summary(served),
                     "one_by_one": summary(base), "batches": srv.stats["batches"],
-                    "max_batch": srv.stats["max_batch"], "bit_exact_equal": bool(same)})
+                    "max_batch": srv.stats["max_batch"],
+                    "launch_ms_max": srv.stats["launch_ms_max"],
+                    "complete_ms_max": srv.stats["complete_ms_max"],
+                    "bit_exact_equal": bool(same),
+                    "cpu_throttled": {"served": thr_served, "one_by_one": thr_base}})
+    gc.unfreeze()
     return {"workload": "poly-multiply requests, N in {2^12,2^14,2^16}, 4-32 limbs, "
                         "operands HBM-resident, Poisson arrivals", "hbm_budget_bytes": budget,
-            "streams": 3, "rates": out}
+            "streams": 3, "completer_wait": "blocking" if blocking_wait else "spin",
+            "cpu_quota": cgroup_cpu(), "rates": out}
 
 
 # ------------------------------------------------------------------ clocks
@@ -532,6 +584,9 @@ def run_case(args):
     hbuild.build()
     N, nl = args.N, args.limbs
     out = {"case": args.case, "N": N, "limbs": nl}
+    if args.case == "serving":
+        print(json.dumps({"case": "serving", "serving": serving_report(torch)}))
+        return 0
     if args.case == "probes":
         for kind in capi.PROBE_KINDS:
             r, ms = capi.hx_probe_int_mul_rate(kind, 8192)
@@ -657,7 +712,7 @@ def main():
                     help="skip the serving report (Poisson arrivals, p50/p99 latency)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--case", default="pipeline",
-                    choices=["pipeline", "fwd", "inv", "tensor", "tensor_inv", "probes"],
+                    choices=["pipeline", "fwd", "inv", "tensor", "tensor_inv", "probes", "serving"],
                     help="pipeline: the contract line; others: one kernel family alone "
                          "(diagnostic line, used for profiling)")
     ap.add_argument("--polys", type=int, default=8, help="polynomials per call for --case fwd/inv")

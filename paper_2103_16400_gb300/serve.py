@@ -90,24 +90,38 @@ class Server:
     """Engine and completer threads + streams; `submit()` is thread-safe and
     returns a Future that resolves to the product (uint64 [limbs][N])."""
 
-    def __init__(self, hbm_budget: int = 64 << 30, streams: int = 3,
-                 max_batch: int = 256, device: int = 0):
+    def __init__(self, hbm_budget: int = 64 << 30, streams=3,
+                 max_batch: int = 256, device: int = 0, blocking_wait: bool = True):
+        """streams: how many CUDA streams to create, or the streams to use
+        (servers that share streams also share the caching allocator's blocks,
+        which the allocator keeps per stream).  blocking_wait: the completer
+        sleeps in the driver until a batch's end event fires (a blocking-sync
+        event) instead of spinning a host core on it."""
         import torch
         self.torch = torch
         self.device = device
         self.budget = int(hbm_budget)
         self.max_batch = max_batch
+        self.blocking_wait = blocking_wait
         torch.cuda.set_device(device)
         capi.load()
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
-        self.free_streams = list(range(streams))
+        if isinstance(streams, int):
+            streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
+        self.streams = list(streams)
+        if not self.streams:
+            raise ValueError("a server needs at least one stream")
+        self.free_streams = list(range(len(self.streams)))
         self.in_use = 0
         self.n_inflight = 0
         self.plans: Dict[Tuple[int, Tuple[int, ...]], capi.Plan] = {}
         self.inbox: "queue.Queue" = queue.Queue()
         self.done_q: "queue.Queue" = queue.Queue()
         self.waiting: "collections.deque[Request]" = collections.deque()
-        self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "launches": 0}
+        # launch_ms_max: the longest host time spent launching one batch
+        # (marshalling, allocation, the ragged call); complete_ms_max: the
+        # longest spent handing one finished batch's results to its futures
+        self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "launches": 0,
+                      "launch_ms_max": 0.0, "complete_ms_max": 0.0}
         self._lock = threading.Lock()            # in_use, free_streams, n_inflight, stats
         self._stop = threading.Event()
         self._threads: List[threading.Thread] = []
@@ -121,10 +135,12 @@ class Server:
             p = self.plans[key] = capi.Plan(N, key[1])
         return p
 
-    def submit(self, req: Request) -> Future:
+    def submit(self, req: Request, arrival: Optional[float] = None) -> Future:
+        """Queue a request; its latency counts from `arrival` (a perf_counter()
+        time, e.g. when a load generator scheduled it) or from now."""
         if req.device_bytes > self.budget:
             raise BudgetError(f"request needs {req.device_bytes} bytes, budget {self.budget}")
-        req.arrival = time.perf_counter()
+        req.arrival = time.perf_counter() if arrival is None else arrival
         self.inbox.put(req)
         return req.future
 
@@ -208,7 +224,12 @@ class Server:
             self.in_use += need
             self.n_inflight += 1
             sid = self.free_streams.pop()
-        self.done_q.put(self._launch(batch, sid, need))
+        t = time.perf_counter()
+        b = self._launch(batch, sid, need)
+        t = (time.perf_counter() - t) * 1e3
+        with self._lock:
+            self.stats["launch_ms_max"] = max(self.stats["launch_ms_max"], t)
+        self.done_q.put(b)
         return True
 
     def _launch(self, reqs: List[Request], sid: int, need: int) -> dict:
@@ -252,7 +273,7 @@ class Server:
             if host_reqs:
                 out_host = torch.empty(int(res_off[-1]), dtype=torch.int64, pin_memory=True)
                 out_host.copy_(res, non_blocking=True)
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(blocking=self.blocking_wait)
             ev.record(stream)
         with self._lock:
             self.stats["batches"] += 1
@@ -282,6 +303,9 @@ class Server:
                         r.result = hv[lo:hi].reshape(r.limbs, r.N).copy()
                     r.done = now
                     r.future.set_result(r.result)
+                t = (time.perf_counter() - now) * 1e3
+                with self._lock:
+                    self.stats["complete_ms_max"] = max(self.stats["complete_ms_max"], t)
             except BaseException as e:
                 self._error = e
                 for r in b["reqs"]:
@@ -306,6 +330,9 @@ def serve_one_by_one(reqs: Sequence[Request], arrivals: Optional[Sequence[float]
     t0 = time.perf_counter()
     for i, r in enumerate(reqs):
         if arrivals is not None:
+            wait = arrivals[i] - (time.perf_counter() - t0)
+            if wait > 1e-4:                       # sleep (not spin) until the arrival
+                time.sleep(wait - 5e-5)
             while time.perf_counter() - t0 < arrivals[i]:
                 pass
             r.arrival = t0 + arrivals[i]

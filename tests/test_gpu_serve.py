@@ -107,3 +107,24 @@ def test_oversized_request_is_refused(hexlib):
     srv = serve.Server(hbm_budget=r.device_bytes - 1, streams=1)
     with pytest.raises(serve.BudgetError):
         srv.submit(r)
+
+
+def test_servers_share_given_streams_and_stamp_given_arrivals(hexlib):
+    """Two servers in turn on the same two caller-made streams give the same
+    bits; a submission stamped with an earlier arrival counts its latency
+    from that time."""
+    import torch
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    reqs = make_requests(12, W.SEED_BASE + 11)
+    got = []
+    for _ in range(2):
+        with serve.Server(hbm_budget=8 << 30, streams=streams) as srv:
+            assert srv.streams == streams
+            t = time.perf_counter() - 0.25
+            rs = clone(reqs)
+            got.append([srv.submit(r, arrival=t).result(timeout=120) for r in rs])
+            assert all(r.arrival == t and r.latency >= 0.25 for r in rs)
+    for a, b in zip(*got):
+        np.testing.assert_array_equal(a, b)
+    with pytest.raises(ValueError):
+        serve.Server(streams=[])
