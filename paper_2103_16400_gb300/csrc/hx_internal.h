@@ -62,6 +62,14 @@ struct hx_plan_s {
     std::vector<std::shared_ptr<hx::TableEntry>> tables;   // one per limb (may repeat)
     hx::LimbDev* d_limbs = nullptr;
     std::vector<hx::LimbDev> h_limbs;
+    // Launch order of the limbs in the fused tensor pass: grid row y
+    // transforms limb d_order[y].  Costliest limbs first (64-bit exact-quotient, then
+    // truncated-quotient, then 32-bit words), stable, permuted within runs of
+    // 64 limbs (the fused tensor pass launches at most 64 at a time), so that
+    // the blocks that finish a pass are the short ones.  Device copy inside
+    // the d_limbs allocation.
+    uint32_t* d_order = nullptr;
+    std::vector<uint32_t> h_order;
     uint64_t device_bytes = 0;
     bool cyclic = false;               // cyclic NTT over omega (else negacyclic over psi)
     hx::NttCfg cfg_fwd{}, cfg_inv{};   // kernel schedules per direction
@@ -77,6 +85,7 @@ bool is_prime_u64(uint64_t n);
 uint64_t powmod_u64(uint64_t a, uint64_t e, uint64_t q);
 uint64_t min_primitive_root(uint64_t N, uint64_t q);
 uint64_t min_primitive_nth_root(uint64_t N, uint64_t q);
+std::vector<uint32_t> launch_order(const std::vector<LimbDev>& limbs);
 NttCfg default_cfg(int logN, bool forward);
 int acquire_tables(int device, uint64_t N, int logN, const std::vector<uint64_t>& moduli,
                    const std::vector<uint64_t>& roots, bool cyclic,

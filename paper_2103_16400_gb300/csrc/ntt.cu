@@ -102,6 +102,7 @@ static cudaError_t launch_pass(const hx_plan_s* plan, const PassCfg& p, uint64_t
     a.out = out;
     a.in = in;
     a.limbs = plan->d_limbs;
+    a.order = nullptr;   // natural order: many short blocks, limbs of both widths mixed
     a.n_limbs = plan->n_limbs;
     a.n_polys = n_polys;
     a.L = L;
@@ -155,6 +156,10 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
 // transforms all three outputs of a ciphertext in one block.
 static int tensor_npf(const PassCfg& p) { return p.np > 1 ? 3 : 1; }
 
+// The plan's launch order permutes limbs within runs of 64, so every chunk of
+// the fused pass's launches maps onto itself.
+static_assert(kTensorLimbs == 64, "launch_order permutes within runs of kTensorLimbs");
+
 bool tensor_fusable(const NttCfg& cfg) {
     const PassCfg& p = cfg.pass[cfg.npass - 1];   // the inverse runs this pass first
     if (p.pipe == 1 || p.logGc != 0) return false;
@@ -177,6 +182,7 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
     a.out = out;
     a.in = nullptr;
     a.limbs = plan->d_limbs;
+    a.order = plan->d_order;   // few long blocks: the costliest limbs start first
     a.n_limbs = plan->n_limbs;
     a.n_polys = 3 * n_ct;
     a.L = L;

@@ -37,6 +37,7 @@ struct PassArgs {
     uint64_t* out;
     const uint64_t* in;
     const LimbDev* limbs;
+    const uint32_t* order;   // grid row -> limb (the plan's launch order), or nullptr: row = limb
     uint32_t n_limbs;
     uint32_t n_polys;
     int L;            // log2 N
@@ -468,7 +469,7 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
 template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false>
 __global__ void HX_PASS_MAXNREG ntt_pass_kernel(PassArgs a) {
     extern __shared__ uint64_t sm[];
-    const uint32_t limb = blockIdx.y;
+    const uint32_t limb = a.order ? a.order[blockIdx.y] : blockIdx.y;
     const uint32_t n_groups = (a.n_polys + NP - 1) / NP;
     const uint32_t poly = (blockIdx.x % n_groups) * NP;
     const uint32_t tile = blockIdx.x / n_groups;

@@ -263,6 +263,19 @@ int acquire_tables(int device, uint64_t N, int logN, const std::vector<uint64_t>
     return HX_OK;
 }
 
+// The launch order of a plan's limbs (see hx_plan_s::d_order): within each
+// run of 64, limbs by decreasing cost of their butterfly, ties in index order.
+std::vector<uint32_t> launch_order(const std::vector<LimbDev>& limbs) {
+    auto cost = [&](uint32_t l) { return limbs[l].narrow ? 0 : limbs[l].trunc ? 1 : 2; };
+    const uint32_t n = (uint32_t)limbs.size();
+    std::vector<uint32_t> order(n);
+    for (uint32_t l = 0; l < n; ++l) order[l] = l;
+    for (uint32_t b = 0; b < n; b += 64)
+        std::stable_sort(order.begin() + b, order.begin() + std::min(n, b + 64),
+                         [&](uint32_t x, uint32_t y) { return cost(x) > cost(y); });
+    return order;
+}
+
 }  // namespace hx
 
 using namespace hx;
@@ -310,17 +323,23 @@ static int plan_create(hx_plan_t* out, uint64_t N, const uint64_t* h_moduli, uin
     }
     p->h_limbs.resize(n_limbs);
     for (uint32_t l = 0; l < n_limbs; ++l) p->h_limbs[l] = p->tables[l]->ld;
-    if (cudaMalloc((void**)&p->d_limbs, n_limbs * sizeof(LimbDev)) != cudaSuccess) {
+    p->h_order = launch_order(p->h_limbs);
+    const size_t limb_bytes = n_limbs * sizeof(LimbDev);
+    const size_t bytes = limb_bytes + n_limbs * sizeof(uint32_t);
+    if (cudaMalloc((void**)&p->d_limbs, bytes) != cudaSuccess) {
         delete p;
         return HX_ERR_NOMEM;
     }
-    if (cudaMemcpy(p->d_limbs, p->h_limbs.data(), n_limbs * sizeof(LimbDev),
+    p->d_order = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(p->d_limbs) + limb_bytes);
+    if (cudaMemcpy(p->d_limbs, p->h_limbs.data(), limb_bytes, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(p->d_order, p->h_order.data(), n_limbs * sizeof(uint32_t),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(p->d_limbs);
         delete p;
         return HX_ERR_CUDA;
     }
-    p->device_bytes = n_limbs * sizeof(LimbDev);
+    p->device_bytes = bytes;
     std::vector<const TableEntry*> seen;
     for (auto& t : p->tables) {
         if (std::find(seen.begin(), seen.end(), t.get()) == seen.end()) {
