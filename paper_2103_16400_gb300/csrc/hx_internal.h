@@ -62,7 +62,8 @@ struct hx_plan_s {
     std::vector<std::shared_ptr<hx::TableEntry>> tables;   // one per limb (may repeat)
     hx::LimbDev* d_limbs = nullptr;
     std::vector<hx::LimbDev> h_limbs;
-    // Launch order of the limbs in the fused tensor pass: grid row y
+    // Launch order of the limbs in the fused tensor pass and the column
+    // passes (fewer, longer blocks than the row passes): grid row y
     // transforms limb d_order[y].  Costliest limbs first (64-bit exact-quotient, then
     // truncated-quotient, then 32-bit words), stable, permuted within runs of
     // 64 limbs (the fused tensor pass launches at most 64 at a time), so that

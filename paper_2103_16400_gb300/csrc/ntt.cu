@@ -102,7 +102,9 @@ static cudaError_t launch_pass(const hx_plan_s* plan, const PassCfg& p, uint64_t
     a.out = out;
     a.in = in;
     a.limbs = plan->d_limbs;
-    a.order = nullptr;   // natural order: many short blocks, limbs of both widths mixed
+    // column passes: fewer, longer blocks (16 elements a thread) -- the costliest
+    // limbs start first; row passes: many short blocks, natural order
+    a.order = p.logGc > 0 ? plan->d_order : nullptr;
     a.n_limbs = plan->n_limbs;
     a.n_polys = n_polys;
     a.L = L;

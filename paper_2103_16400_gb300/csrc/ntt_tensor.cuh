@@ -27,7 +27,8 @@ template <int LOG_R, int K, bool TWS, int NPF>
 __global__ void __maxnreg__(NPF == 3 ? 96 : (LOG_R == 4 ? 72 : 64))
     ntt_tensor_inv_kernel(PassArgs a, TensorIn t) {
     extern __shared__ uint64_t sm[];
-    const uint32_t limb = a.order[t.limb0 + blockIdx.y], li = limb - t.limb0;
+    const uint32_t limb = a.order ? a.order[t.limb0 + blockIdx.y] : t.limb0 + blockIdx.y;
+    const uint32_t li = limb - t.limb0;
     const uint32_t G = (NPF == 3 ? 1 : 3) * t.n_ct;
     const uint32_t g = blockIdx.x % G, tile = blockIdx.x / G;
     const uint32_t k = NPF == 3 ? 0 : g / t.n_ct, p = g % t.n_ct;
