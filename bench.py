@@ -88,14 +88,15 @@ def slots_per_butterfly(q):
 
 #: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, both pass launches)
 #: of one forward call over 4 polynomials x 32 mixed limbs at N = 65536, from
-#: ncu --set full captures of that call under each schedule listed; reported
+#: ncu captures (dram__bytes_* metrics, the current kernels with the column
+#: passes' limb launch order) of that call under each schedule listed; reported
 #: only when the tuned forward schedule is one of them (other kernels, other
 #: traffic).  Keyed by the schedule's JSON.
 FWD_TRAFFIC_BYTES = {
-    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]": 67256320 + 17201152 + 100655616 + 17272064,
-    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 1]]": 67247872 + 16849920 + 100657664 + 17978624,
-    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]": 67316992 + 22987008 + 100586752 + 17123840,
-    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]": 67325952 + 22792448 + 100587008 + 17210880,
+    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]": 67257856 + 17679360 + 100657408 + 14364416,
+    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 1]]": 67254784 + 17325312 + 100657152 + 14397440,
+    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]": 67323136 + 24393472 + 100595200 + 14092032,
+    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]": 67322112 + 23800576 + 100591104 + 14021376,
 }
 
 
