@@ -68,3 +68,29 @@ def test_tuning_one_direction_keeps_the_other(hexlib, tmp_path, monkeypatch):
         inv = tune.tune_tensor(plan, 1, s, iters=1)["inverse"]
         assert [list(p) for p in plan.schedule(plan.FORWARD)] == f
         assert [list(p) for p in plan.schedule(plan.INVERSE)] == inv
+
+
+def test_launch_order_many_mixed_limbs(hexlib):
+    """70 limbs of four widths (30-bit words, truncated- and exact-quotient
+    64-bit words): column passes launch them costliest first within runs of
+    64, so under every run of the order and each covering
+    schedule must still transform every limb exactly once, bit-exact."""
+    N = 1 << 14
+    moduli = W.mixed_width_primes(70, widths=(30, 50, 60, 62))
+    x = W.poly_batch(W.SEED_BASE + 960, 1, 2, moduli, N)
+    fwd_exp = oracle.ntt_forward(x, moduli)
+    plan = capi.Plan(N, moduli)
+    dx, dy, dz = to_device(x), empty(x.shape), empty(x.shape)
+    n = 0
+    for sched in tune.covering(plan):
+        plan.set_schedule(sched)
+        dy.fill_(0)
+        dz.fill_(0)
+        capi.hx_ntt_forward(plan, dy, dx, 2, 1, 1)
+        capi.hx_ntt_inverse(plan, dz, dy, 2, 1, 1)
+        if not np.array_equal(to_host(dy), fwd_exp):
+            pytest.fail(f"forward differs under schedule {sched}")
+        if not np.array_equal(to_host(dz), x):
+            pytest.fail(f"inverse differs under schedule {sched}")
+        n += 1
+    assert n >= 4

@@ -127,3 +127,21 @@ def test_rejects_bad_arguments(hexlib):
     with pytest.raises(capi.HexError):          # scalar >= q
         capi.hx_tensor_fma_inverse(plan, R[0], R[1], R[2], A[0], A[1], A[2], A[3], bad,
                                    E[0], E[1], E[2], 1, 4)
+
+
+def test_launch_order_two_pass_many_limbs(hexlib):
+    """Two-pass schedules at N = 2^14 with 70 limbs of four widths: the fused
+    pass (two launches of up to 64 limbs) and the column pass both take the
+    limbs costliest first; every result must be the oracle's."""
+    N = 1 << 14
+    moduli = W.mixed_width_primes(70, widths=(30, 50, 60, 62))
+    A, E, s = operands(W.SEED_BASE + 790, 1, moduli, N, 4)
+    exp = expected(A, E, s, moduli)
+    plan = capi.Plan(N, moduli)
+    scheds = [sc for sc in tune.covering(plan) if len(sc) == 2][:6]
+    assert scheds
+    for sched in scheds:
+        plan.set_schedule(sched)
+        for got, e in zip(run_fused(plan, A, E, s, 1, 4), exp):
+            if not np.array_equal(got, e):
+                pytest.fail(f"differs under schedule {sched}")
