@@ -73,8 +73,8 @@ def test_tuning_one_direction_keeps_the_other(hexlib, tmp_path, monkeypatch):
 def test_launch_order_many_mixed_limbs(hexlib):
     """70 limbs of four widths (30-bit words, truncated- and exact-quotient
     64-bit words): column passes launch them costliest first within runs of
-    64, so under every run of the order and each covering
-    schedule must still transform every limb exactly once, bit-exact."""
+    64; under each covering schedule every limb must still be transformed
+    exactly once, bit-exact."""
     N = 1 << 14
     moduli = W.mixed_width_primes(70, widths=(30, 50, 60, 62))
     x = W.poly_batch(W.SEED_BASE + 960, 1, 2, moduli, N)
