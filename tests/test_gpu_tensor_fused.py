@@ -130,11 +130,12 @@ def test_rejects_bad_arguments(hexlib):
 
 
 def test_launch_order_two_pass_many_limbs(hexlib):
-    """Two-pass schedules at N = 2^14 with 70 limbs of four widths: the fused
-    pass (two launches of up to 64 limbs) and the column pass both take the
-    limbs costliest first; every result must be the oracle's."""
+    """Two-pass schedules at N = 2^14 with 70 limbs of the 30/50/60-bit mix
+    (the tensor's FMA takes moduli below 2^61): the fused pass (two launches
+    of up to 64 limbs) and the column pass both take the 64-bit-word limbs
+    first; every result must be the oracle's."""
     N = 1 << 14
-    moduli = W.mixed_width_primes(70, widths=(30, 50, 60, 62))
+    moduli = W.mixed_width_primes(70)
     A, E, s = operands(W.SEED_BASE + 790, 1, moduli, N, 4)
     exp = expected(A, E, s, moduli)
     plan = capi.Plan(N, moduli)
