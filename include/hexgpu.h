@@ -361,10 +361,15 @@ int hx_batch_run_static(const hx_ragged_item* h_items, uint32_t n_items, uint32_
  *   d_workspace: caller-owned device memory, 256-byte aligned, at least the
  *   size hx_polymul_ragged_workspace reports (twice the operand size plus
  *   32 bytes per tile); it holds the spectra, the tile lists and the work
- *   counters, so the library allocates nothing.  A workspace may be reused
- *   by calls ordered on one stream, not by concurrent ones.
+ *   counters, so the library allocates no device memory.  A workspace may be
+ *   reused by calls ordered on one stream, not by concurrent ones.  The tile
+ *   lists are written on the host into page-locked staging buffers that the
+ *   library keeps (a pool grown on demand, each reused once its upload has
+ *   completed, held for the life of the process) and uploaded asynchronously
+ *   on `stream`; the call returns without waiting for the GPU.
  *   Errors: HX_ERR_NULL, HX_ERR_ALIGN, HX_ERR_ARG, HX_ERR_MODULUS,
- *   HX_ERR_CAPACITY (workspace too small), HX_ERR_CUDA. */
+ *   HX_ERR_CAPACITY (workspace too small), HX_ERR_NOMEM (no page-locked
+ *   staging), HX_ERR_CUDA. */
 typedef struct hx_polymul_item {
     hx_plan_t plan;
     const uint64_t* d_a;

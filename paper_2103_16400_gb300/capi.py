@@ -9,6 +9,7 @@ HexError carrying the library's own message.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 import threading
 from typing import Optional, Sequence
@@ -205,11 +206,45 @@ def polymul_items(items):
                                         for p, a, b, r, n in items]), len(items)
 
 
+def polymul_items_array(plans, a_ptrs, b_ptrs, r_ptrs, n_polys=1):
+    """The same hx_polymul_item array built column by column in numpy (for a
+    server launching hundreds of items at once): plan handles and device
+    pointers as integer sequences or arrays, n_polys a scalar or sequence.
+    Returns (array, n), accepted wherever polymul_items()'s pair is."""
+    import numpy as np
+    n = len(plans)
+    arr = np.zeros(n, _polymul_dtype())
+    arr["plan"] = plans
+    arr["d_a"] = a_ptrs
+    arr["d_b"] = b_ptrs
+    arr["d_result"] = r_ptrs
+    arr["n_polys"] = n_polys
+    return arr, n
+
+
+@functools.lru_cache(maxsize=None)
+def _polymul_dtype():
+    import numpy as np
+    dt = np.dtype([("plan", "<u8"), ("d_a", "<u8"), ("d_b", "<u8"), ("d_result", "<u8"),
+                   ("n_polys", "<u4"), ("reserved", "<u4")])
+    assert dt.itemsize == ctypes.sizeof(PolymulItem)
+    return dt
+
+
+def _items_ptr(arr):
+    """Address of an item array from polymul_items() or polymul_items_array()."""
+    if hasattr(arr, "ctypes") and hasattr(arr, "dtype"):     # numpy array
+        if not arr.flags["C_CONTIGUOUS"] or arr.dtype != _polymul_dtype():
+            raise ValueError("item array must be a contiguous polymul_items_array()")
+        return VP(arr.ctypes.data)
+    return ctypes.cast(arr, VP)
+
+
 def hx_polymul_ragged_workspace(items) -> int:
     arr, n = items if isinstance(items, tuple) else polymul_items(items)
     out = U64()
     _check("hx_polymul_ragged_workspace", load().hx_polymul_ragged_workspace(
-        ctypes.cast(arr, VP), n, ctypes.byref(out)))
+        _items_ptr(arr), n, ctypes.byref(out)))
     return out.value
 
 
@@ -217,7 +252,7 @@ def hx_polymul_ragged(items, workspace, workspace_bytes: int, stream=None):
     """items: (plan, a, b, result, n_polys) tuples or a polymul_items() pair."""
     arr, n = items if isinstance(items, tuple) else polymul_items(items)
     _check("hx_polymul_ragged", load().hx_polymul_ragged(
-        ctypes.cast(arr, VP), n, ptr(workspace), workspace_bytes, _stream(stream)))
+        _items_ptr(arr), n, ptr(workspace), workspace_bytes, _stream(stream)))
 
 
 def hx_batch_run_static(items, direction: int = 1, input_mod_factor: int = 1,

@@ -492,6 +492,61 @@ extern "C" int hx_polymul_ragged_workspace(const hx_polymul_item* items, uint32_
     return HX_OK;
 }
 
+// Page-locked host staging for the descriptor lists of hx_polymul_ragged.  A
+// copy from pageable memory would first wait for the stream's earlier work and
+// then pass through the driver's own staging buffers; from page-locked memory
+// it is one asynchronous DMA.  A buffer is handed out again only once the
+// event recorded after the copy that last read it has completed; buffers grow
+// to the largest list seen and live as long as the process.
+struct DescStaging {
+    unsigned char* buf = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    int device = -1;
+    bool busy = false;
+};
+static std::mutex g_stage_mu;
+static std::vector<DescStaging*> g_stage;
+
+static DescStaging* staging_acquire(size_t bytes, int dev) {
+    std::lock_guard<std::mutex> g(g_stage_mu);
+    DescStaging* pick = nullptr;
+    for (DescStaging* st : g_stage) {
+        if (st->device != dev || st->busy) continue;
+        if (cudaEventQuery(st->done) != cudaSuccess) continue;   // its copy is in flight
+        if (!pick || (st->cap >= bytes && (pick->cap < bytes || st->cap < pick->cap))) pick = st;
+    }
+    if (!pick) {
+        pick = new (std::nothrow) DescStaging();
+        if (!pick) return nullptr;
+        if (cudaEventCreateWithFlags(&pick->done, cudaEventDisableTiming) != cudaSuccess) {
+            delete pick;
+            return nullptr;
+        }
+        pick->device = dev;
+        g_stage.push_back(pick);
+    }
+    if (pick->cap < bytes) {
+        size_t cap = 1 << 16;
+        while (cap < bytes) cap <<= 1;
+        if (pick->buf) cudaFreeHost(pick->buf);
+        pick->buf = nullptr;
+        pick->cap = 0;
+        if (cudaHostAlloc((void**)&pick->buf, cap, cudaHostAllocDefault) != cudaSuccess) {
+            pick->buf = nullptr;
+            return nullptr;
+        }
+        pick->cap = cap;
+    }
+    pick->busy = true;
+    return pick;
+}
+
+static void staging_release(DescStaging* st) {
+    std::lock_guard<std::mutex> g(g_stage_mu);
+    st->busy = false;
+}
+
 extern "C" int hx_polymul_ragged(const hx_polymul_item* items, uint32_t n_items, void* d_workspace,
                                  uint64_t workspace_bytes, hx_stream_t stream) {
     if (!items || !d_workspace) return HX_ERR_NULL;
@@ -504,9 +559,13 @@ extern "C" int hx_polymul_ragged(const hx_polymul_item* items, uint32_t n_items,
     unsigned char* ws = (unsigned char*)d_workspace;
     uint32_t* counters = (uint32_t*)ws;
     // descriptors, in launch order: fwd A, fwd B, inv A, inv B, then products
-    std::vector<unsigned char> host((L.fA + L.fB + L.iA + L.iB) * sizeof(RagTile) +
-                                    L.mul * sizeof(MulTile));
-    RagTile* fA = (RagTile*)host.data();
+    const size_t host_bytes =
+        (L.fA + L.fB + L.iA + L.iB) * sizeof(RagTile) + L.mul * sizeof(MulTile);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    DescStaging* stage = staging_acquire(host_bytes, dev);
+    if (!stage) return HX_ERR_NOMEM;
+    RagTile* fA = (RagTile*)stage->buf;
     RagTile* fB = fA + L.fA;
     RagTile* iA = fB + L.fB;
     RagTile* iB = iA + L.iA;
@@ -550,10 +609,13 @@ extern "C" int hx_polymul_ragged(const hx_polymul_item* items, uint32_t n_items,
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(counters, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return HX_ERR_CUDA;
-    if (cudaMemcpyAsync(ws + L.tiles_off, host.data(), host.size(), cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-        return HX_ERR_CUDA;
+    const bool staged =
+        cudaMemsetAsync(counters, 0, 4 * sizeof(uint32_t), s) == cudaSuccess &&
+        cudaMemcpyAsync(ws + L.tiles_off, stage->buf, host_bytes, cudaMemcpyHostToDevice, s) ==
+            cudaSuccess &&
+        cudaEventRecord(stage->done, s) == cudaSuccess;
+    if (!staged) return HX_ERR_CUDA;   // stays busy: an enqueued copy may still read it
+    staging_release(stage);
     const RagTile* dt = (const RagTile*)(ws + L.tiles_off);
     const int gf = rag_grid(true), gi = rag_grid(false);
     auto pass = [&](bool fwd, const RagTile* t, uint64_t cnt, uint32_t* ctr, int grid) {

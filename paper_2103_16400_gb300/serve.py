@@ -140,6 +140,8 @@ class Server:
         time, e.g. when a load generator scheduled it) or from now."""
         if req.device_bytes > self.budget:
             raise BudgetError(f"request needs {req.device_bytes} bytes, budget {self.budget}")
+        if type(req.moduli) is not tuple:
+            req.moduli = tuple(int(q) for q in req.moduli)   # the plan table's key form
         req.arrival = time.perf_counter() if arrival is None else arrival
         self.inbox.put(req)
         return req.future
@@ -236,36 +238,41 @@ class Server:
         torch = self.torch
         stream = self.streams[sid]
         dev_name = f"cuda:{self.device}"
-        sizes = [r.limbs * r.N for r in reqs]
-        res_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        n = len(reqs)
+        sizes = np.fromiter((r.limbs * r.N for r in reqs), np.int64, n)
+        res_off = np.zeros(n + 1, np.int64)
+        np.cumsum(sizes, out=res_off[1:])
         host_reqs = [k for k, r in enumerate(reqs) if not r.resident]
         with torch.cuda.stream(stream):
             res = torch.empty(int(res_off[-1]), dtype=torch.int64, device=dev_name)
             staged = pinned = None
-            in_off = {}
+            a_ptr = [0] * n
+            b_ptr = [0] * n
             if host_reqs:
                 # all host operands through one pinned buffer and one upload
-                total = 2 * sum(sizes[k] for k in host_reqs)
+                total = 2 * int(sizes[host_reqs].sum())
                 pinned = torch.empty(total, dtype=torch.int64, pin_memory=True)
                 pv = pinned.numpy().view(np.uint64)
+                staged = torch.empty(total, dtype=torch.int64, device=dev_name)
+                base = staged.data_ptr()
                 o = 0
                 for k in host_reqs:
-                    r, s = reqs[k], sizes[k]
-                    pv[o:o + s] = r.a.reshape(-1)
-                    pv[o + s:o + 2 * s] = r.b.reshape(-1)
-                    in_off[k] = o
-                    o += 2 * s
-                staged = pinned.to(dev_name, non_blocking=True)
-            items = []
+                    r, sz = reqs[k], int(sizes[k])
+                    pv[o:o + sz] = r.a.reshape(-1)
+                    pv[o + sz:o + 2 * sz] = r.b.reshape(-1)
+                    a_ptr[k], b_ptr[k] = base + 8 * o, base + 8 * (o + sz)
+                    o += 2 * sz
+                staged.copy_(pinned, non_blocking=True)
+            plans = self.plans
+            handles = []
             for k, r in enumerate(reqs):
-                out = res[int(res_off[k]):int(res_off[k + 1])]
+                p = plans.get((r.N, r.moduli))
+                handles.append((p if p is not None else self.plan(r.N, r.moduli)).handle)
                 if r.resident:
-                    a, b = r.a, r.b
-                else:
-                    o, s = in_off[k], sizes[k]
-                    a, b = staged[o:o + s], staged[o + s:o + 2 * s]
-                items.append((self.plan(r.N, r.moduli), a, b, out, 1))
-            arr = capi.polymul_items(items)
+                    a_ptr[k], b_ptr[k] = r.a.data_ptr(), r.b.data_ptr()
+            # results back to back in `res`; operands read in place
+            arr = capi.polymul_items_array(handles, a_ptr, b_ptr,
+                                           res.data_ptr() + 8 * res_off[:-1])
             wsb = capi.hx_polymul_ragged_workspace(arr)
             ws = torch.empty(wsb, dtype=torch.uint8, device=dev_name)
             capi.hx_polymul_ragged(arr, ws, wsb, stream.cuda_stream)
@@ -277,10 +284,10 @@ class Server:
             ev.record(stream)
         with self._lock:
             self.stats["batches"] += 1
-            self.stats["requests"] += len(reqs)
+            self.stats["requests"] += n
             self.stats["launches"] += 5
-            self.stats["max_batch"] = max(self.stats["max_batch"], len(reqs))
-        work = (res, res_off, out_host, staged, pinned, ws)
+            self.stats["max_batch"] = max(self.stats["max_batch"], n)
+        work = (res, sizes, out_host, staged, pinned, ws)
         return {"reqs": reqs, "work": work, "event": ev, "sid": sid, "bytes": need}
 
     # ------------------------------------------------------------ completer
@@ -293,14 +300,17 @@ class Server:
             try:
                 b["event"].synchronize()
                 now = time.perf_counter()
-                res, res_off, out_host, _, _, _ = b["work"]
+                res, sizes, out_host, _, _, _ = b["work"]
+                parts = res.split(sizes.tolist())        # one view per request
                 hv = out_host.numpy().view(np.uint64) if out_host is not None else None
-                for k, r in enumerate(b["reqs"]):
-                    lo, hi = int(res_off[k]), int(res_off[k + 1])
+                lo = 0
+                for r, part in zip(b["reqs"], parts):
+                    hi = lo + part.numel()
                     if r.resident:
-                        r.result = res[lo:hi].view(r.limbs, r.N)
+                        r.result = part.view(r.limbs, r.N)
                     else:
                         r.result = hv[lo:hi].reshape(r.limbs, r.N).copy()
+                    lo = hi
                     r.done = now
                     r.future.set_result(r.result)
                 t = (time.perf_counter() - now) * 1e3
