@@ -122,7 +122,7 @@ class Server:
         # longest spent handing one finished batch's results to its futures
         self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "launches": 0,
                       "launch_ms_max": 0.0, "complete_ms_max": 0.0}
-        self._lock = threading.Lock()            # in_use, free_streams, n_inflight, stats
+        self._lock = threading.Lock()   # in_use, free_streams, n_inflight, stats; _error vs submit
         self._stop = threading.Event()
         self._threads: List[threading.Thread] = []
         self._error: Optional[BaseException] = None
@@ -143,7 +143,10 @@ class Server:
         if type(req.moduli) is not tuple:
             req.moduli = tuple(int(q) for q in req.moduli)   # the plan table's key form
         req.arrival = time.perf_counter() if arrival is None else arrival
-        self.inbox.put(req)
+        with self._lock:
+            if self._error is not None:
+                raise RuntimeError("the server stopped after an error") from self._error
+            self.inbox.put(req)
         return req.future
 
     def start(self) -> "Server":
@@ -178,10 +181,13 @@ class Server:
 
     # ------------------------------------------------------------ engine
     def _fail(self, e: BaseException):
-        self._error = e
+        with self._lock:                  # no submission slips in after the drain
+            self._error = e
+            self._drain_inbox()
         for r in list(self.waiting):
             if not r.future.done():
                 r.future.set_exception(e)
+        self.waiting.clear()
 
     def _run(self):
         self.torch.cuda.set_device(self.device)
@@ -227,7 +233,19 @@ class Server:
             self.n_inflight += 1
             sid = self.free_streams.pop()
         t = time.perf_counter()
-        b = self._launch(batch, sid, need)
+        try:
+            b = self._launch(batch, sid, need)
+        except BaseException as e:
+            # the batch never reached the GPU: fail its requests, give back
+            # its budget and stream, then stop the engine (_run fails the rest)
+            for r in batch:
+                if not r.future.done():
+                    r.future.set_exception(e)
+            with self._lock:
+                self.in_use -= need
+                self.n_inflight -= 1
+                self.free_streams.append(sid)
+            raise
         t = (time.perf_counter() - t) * 1e3
         with self._lock:
             self.stats["launch_ms_max"] = max(self.stats["launch_ms_max"], t)

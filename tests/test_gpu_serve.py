@@ -128,3 +128,26 @@ def test_servers_share_given_streams_and_stamp_given_arrivals(hexlib):
         np.testing.assert_array_equal(a, b)
     with pytest.raises(ValueError):
         serve.Server(streams=[])
+
+
+def test_launch_failure_fails_its_requests_and_stops_the_server(hexlib, monkeypatch):
+    """A batch whose launch raises (an error injected on the host, before any
+    kernel runs): its requests and the waiting ones get the error, later
+    submissions are refused, and stop() re-raises it."""
+    from paper_2103_16400_gb300 import capi
+
+    def broken(*args, **kwargs):
+        raise capi.HexError("hx_polymul_ragged", -7, "injected")
+
+    monkeypatch.setattr(capi, "hx_polymul_ragged", broken)
+    reqs = make_requests(6, W.SEED_BASE + 13)
+    srv = serve.Server(hbm_budget=8 << 30, streams=1).start()
+    futs = [srv.submit(r) for r in reqs]
+    for f in futs:
+        with pytest.raises(capi.HexError):
+            f.result(timeout=60)
+    with pytest.raises(RuntimeError):
+        srv.submit(clone(reqs)[0])
+    with pytest.raises(capi.HexError):
+        srv.stop()
+    assert srv.in_use == 0 and srv.n_inflight == 0
