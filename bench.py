@@ -86,6 +86,44 @@ def slots_per_butterfly(q):
     return SLOTS_WIDE_TRUNC if q < (1 << 61) else SLOTS_WIDE
 
 
+#: IMAD slots of the ciphertext tensor's element-wise step per coefficient
+#: position (three outputs), in the same units.  It takes four modular
+#: products (d1's two summed before one reduction) and three Shoup FMAs.
+#: 64-bit words: a 64x64-bit product is its exact high word (11) and low
+#: word (one full and two low halves, 5); a Barrett reduction (Algorithm
+#: "Barrett Reduction": c3 = high word of c1 k, then d - c3 q mod 2^64) is
+#: 11 + 5; so d0 = d2 = 16 + 16, d1 = 2 * 16 + 16, and an FMA (s a - Q q
+#: with Q the high word of s' a) 5 + 11 + 5: 32 + 48 + 32 + 3 * 21 = 175.
+#: 32-bit words: a product is one full 32x32 (3), a reduction one high half
+#: and one low half (2 + 1), an FMA 1 + 2 + 1: 6 + 9 + 6 + 3 * 4 = 33.
+SLOTS_TENSOR_WIDE, SLOTS_TENSOR_NARROW = 175, 33
+
+
+def slots_per_tensor_position(q):
+    return SLOTS_TENSOR_NARROW if q < (1 << 30) else SLOTS_TENSOR_WIDE
+
+
+#: DRAM bytes (read + write) of one launch of the fused tensor / first
+#: inverse pass over one ciphertext pair at N = 65536 x 32 mixed limbs, from
+#: an ncu capture of the current kernel, keyed by (kernel, that pass of the
+#: inverse schedule).
+FUSED_TRAFFIC_BYTES = {
+    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[7, 9, 1, 0, 3, 0, 2]"): 151025152 + 22551296,
+}
+
+
+def kernel_slots(kid, N, moduli, n_ct=1):
+    """Algorithmic IMAD slots of one launch of a timed kernel in the step:
+    a pass over its K stages (four polynomials forward, three inverse), or
+    the fused pass (the element-wise step plus its K inverse stages on three
+    polynomials per ciphertext pair)."""
+    kind, fwd, K = kid & 3, (kid >> 2) & 1, (kid >> 7) & 31
+    bfly = sum(N // 2 * K * slots_per_butterfly(q) for q in moduli)
+    if kind == 2:
+        return n_ct * (3 * bfly + sum(N * slots_per_tensor_position(q) for q in moduli))
+    return (4 if fwd else 3) * n_ct * bfly
+
+
 #: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, both pass launches)
 #: of one forward call over 4 polynomials x 32 mixed limbs at N = 65536, from
 #: ncu captures (dram__bytes_* metrics, the current kernels with the column
@@ -756,6 +794,8 @@ def main():
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     launches0 = capi.hx_launch_count()
+    capi.hx_timing_read(64)                    # nothing left over
+    capi.hx_timing_enable(True, 4 * args.steps + 64)
     with ClockSampler(local) as clocks:
         t0.record(stream)
         for i in range(args.steps):
@@ -763,6 +803,8 @@ def main():
         t1.record(stream)
         torch.cuda.synchronize()
     launches = capi.hx_launch_count() - launches0
+    capi.hx_timing_enable(False)
+    timed = capi.hx_timing_read(4 * args.steps + 64)
     total_ms = t0.elapsed_time(t1)
     fwd_ms = [a.elapsed_time(b) for a, b in step.fwd_events]
     inv_ms = [a.elapsed_time(b) for a, b in step.inv_events]
@@ -794,6 +836,46 @@ def main():
                 "peak_source": "hx_probe_int_mul_rate mad.lo.u32 (1 slot), measured live",
                 "schedules": {k: v.get("forward" if k == "forward" else "inverse")
                               for k, v in getattr(step, "tuned", {}).items()}}
+
+    # every kernel of the step timed live (library events around each launch
+    # inside the timed region); the roofline object is the dominant kernel's
+    kernels = {}
+    for kid, ms in timed:
+        k = kernels.setdefault(kid, {"kernel": capi.hx_kernel_name(kid), "launches": 0,
+                                     "total_ms": 0.0})
+        k["launches"] += 1
+        k["total_ms"] += ms
+    timed_total = sum(k["total_ms"] for k in kernels.values()) or 1.0
+    for kid, k in kernels.items():
+        k["avg_us"] = k["total_ms"] / k["launches"] * 1e3
+        k["share"] = k["total_ms"] / timed_total
+        k["alg_slots_per_launch"] = kernel_slots(kid, N, wl.moduli)
+        k["achieved_T_slots_per_s"] = k["alg_slots_per_launch"] / (k["avg_us"] * 1e-6) / 1e12
+        k["frac"] = k["achieved_T_slots_per_s"] * 1e12 / imad_rate
+    roofline_forward_call = roofline
+    if kernels:
+        dom_id = max(kernels, key=lambda i: kernels[i]["total_ms"])
+        dom = kernels[dom_id]
+        inv_sched = getattr(step, "tuned", {}).get("inverse", {}).get("inverse")
+        dom_traffic = None
+        if (dom_id & 3) == 2 and inv_sched and (N, nl) == (1 << 16, 32):
+            dom_traffic = FUSED_TRAFFIC_BYTES.get((dom["kernel"], json.dumps(inv_sched[-1])))
+        dom_bytes = (10 if (dom_id & 3) == 2 else 2 * (4 if (dom_id >> 2) & 1 else 3)) * 8 * N * nl
+        roofline = {"bound": "alu", "achieved": dom["achieved_T_slots_per_s"],
+                    "peak": imad_rate / 1e12, "unit": "T IMAD-slot/s", "frac": dom["frac"],
+                    "traffic": dom_traffic,
+                    "traffic_unit": "DRAM bytes per launch (ncu, same kernel and workload)",
+                    "kernel": dom["kernel"], "launches": dom["launches"],
+                    "avg_launch_us": dom["avg_us"], "share_of_timed_kernels": dom["share"],
+                    "alg_slots_per_launch": dom["alg_slots_per_launch"],
+                    "alg_bytes_per_launch": dom_bytes,
+                    "hbm_gbs_algorithmic": dom_bytes / (dom["avg_us"] * 1e-6) / 1e9,
+                    "dram_gbs_measured": (dom_traffic / (dom["avg_us"] * 1e-6) / 1e9
+                                          if dom_traffic else None),
+                    "peak_source": roofline_forward_call["peak_source"],
+                    "timing": "CUDA events recorded by the library around every launch, "
+                              "on the launching stream, over the timed region",
+                    "schedules": roofline_forward_call["schedules"]}
 
     # end to end through the public API with host buffers: every step uploads
     # its inputs from pinned host memory and downloads its three results; the
@@ -834,6 +916,8 @@ def main():
                              f"{args.sets * 7 * nl * N * 8 / 2**20:.0f} MiB of inputs > 129 MB L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline,
+            "roofline_forward_call": roofline_forward_call,
+            "kernels": sorted(kernels.values(), key=lambda k: -k["total_ms"]),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                     "ms_per_step": e2e_ms / e2e_steps,

@@ -412,6 +412,35 @@ int hx_polymul_ragged(const hx_polymul_item* h_items, uint32_t n_items, void* d_
  * Errors: HX_ERR_NULL, HX_ERR_ARG, HX_ERR_NOMEM, HX_ERR_CUDA.
  */
 uint64_t hx_launch_count(void);
+
+/* Per-launch timing (instrumentation; off by default).
+ *
+ * hx_timing_enable(1, capacity): every NTT pass kernel and fused tensor pass
+ *   that the library launches from now on records a CUDA event before and
+ *   after itself on its own stream, for up to `capacity` launches (1 ..
+ *   2^20; further launches are not recorded).  The events are created here,
+ *   so recording allocates nothing.  hx_timing_enable(0, 0) stops recording;
+ *   what was recorded stays until read.  Errors: HX_ERR_ARG, HX_ERR_CUDA.
+ * hx_timing_read: waits for the recorded launches to finish, writes up to
+ *   `cap` of them in launch order to h_out (kernel id and duration in ms),
+ *   sets *n_out to the number written and clears the record (all of it,
+ *   even beyond `cap`).  Must not run while another thread is launching
+ *   library kernels that it wants recorded.  Errors: HX_ERR_NULL, HX_ERR_CUDA
+ *   (an event failed; the others are still written).
+ * hx_kernel_name: the kernel's name with its template arguments, as CUDA
+ *   tools print it (e.g. "ntt_pass_kernel<1, 0, 3, 8, 1, 0>"), into buf.
+ *   Errors: HX_ERR_NULL, HX_ERR_ARG (unknown id), HX_ERR_CAPACITY (len too
+ *   small). */
+typedef struct hx_launch_time {
+    uint32_t kernel;   /* kernel id, for hx_kernel_name */
+    uint32_t reserved;
+    float ms;          /* launch duration between its two events */
+    float reserved2;
+} hx_launch_time;
+
+int hx_timing_enable(int on, uint32_t capacity);
+int hx_timing_read(hx_launch_time* h_out, uint32_t cap, uint32_t* n_out);
+int hx_kernel_name(uint32_t kernel, char* buf, uint32_t len);
 int hx_probe_int_mul_rate(uint32_t kind, uint32_t iters, double* ops_per_s, float* ms,
                           hx_stream_t stream);
 int hx_probe_butterfly_rate(uint32_t variant, uint32_t iters, uint64_t q,

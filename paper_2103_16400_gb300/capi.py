@@ -60,6 +60,9 @@ _SIGS = {
                                 ctypes.POINTER(ctypes.c_float), VP],
     "hx_probe_copy_rate": [VP, VP, U64, U32, U32, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_float), VP],
+    "hx_timing_enable": [I32, U32],
+    "hx_timing_read": [VP, U32, ctypes.POINTER(U32)],
+    "hx_kernel_name": [U32, ctypes.c_char_p, U32],
 }
 _RESTYPES = {"hx_strerror": ctypes.c_char_p, "hx_launch_count": U64}
 
@@ -426,3 +429,29 @@ def hx_probe_copy_rate(dst, src, nbytes: int, iters: int = 10, blocks_per_sm: in
         ptr(dst), ptr(src), nbytes, iters, blocks_per_sm, ctypes.byref(r), ctypes.byref(t),
         _stream(stream)))
     return r.value, t.value
+
+
+class LaunchTime(ctypes.Structure):
+    """hx_launch_time: one recorded launch."""
+    _fields_ = [("kernel", U32), ("reserved", U32), ("ms", ctypes.c_float),
+                ("reserved2", ctypes.c_float)]
+
+
+def hx_timing_enable(on: bool, capacity: int = 0):
+    """Start (with room for `capacity` launches) or stop per-launch timing."""
+    _check("hx_timing_enable", load().hx_timing_enable(1 if on else 0, capacity))
+
+
+def hx_timing_read(cap: int = 1 << 16):
+    """Recorded launches since the last read, in launch order, as
+    (kernel id, ms) pairs; waits for them to finish and clears the record."""
+    buf = (LaunchTime * cap)()
+    n = U32()
+    _check("hx_timing_read", load().hx_timing_read(ctypes.cast(buf, VP), cap, ctypes.byref(n)))
+    return [(buf[i].kernel, buf[i].ms) for i in range(n.value)]
+
+
+def hx_kernel_name(kernel: int) -> str:
+    buf = ctypes.create_string_buffer(96)
+    _check("hx_kernel_name", load().hx_kernel_name(kernel, buf, 96))
+    return buf.value.decode()

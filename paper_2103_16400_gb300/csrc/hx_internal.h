@@ -80,6 +80,13 @@ namespace hx {
 
 // probe.cu: counts kernel launches made by this library (all entry points)
 void count_launch(uint64_t n = 1);
+// probe.cu: per-launch timing (hx_timing_enable); timing_begin returns 0 when
+// off or full, else a slot to pass to timing_end after the launch.  Kernel
+// ids: bits 0-1 kind (0 per-tile pass, 1 persistent pass, 2 fused tensor
+// pass), 2 forward, 3 column, 4-6 logR, 7-11 K, 12-13 polynomials (outputs
+// for the fused pass) per block, 14 staged twiddles.
+uint32_t timing_begin(cudaStream_t s, uint32_t kernel);
+void timing_end(uint32_t slot, cudaStream_t s);
 
 // plan.cpp
 bool is_prime_u64(uint64_t n);

@@ -93,6 +93,13 @@ static int resident_blocks(PassKernel k, int threads, size_t smem, int* sms) {
     return it->second.first;
 }
 
+// Kernel id of a pass for launch timing (layout in hx_internal.h).
+static uint32_t pass_kernel_id(bool fwd, const PassCfg& p) {
+    return (p.pipe == 1 ? 1u : 0u) | (fwd ? 4u : 0u) | (p.logGc > 0 ? 8u : 0u) |
+           ((uint32_t)p.logR << 4) | ((uint32_t)p.K << 7) | ((uint32_t)p.np << 12) |
+           (p.pipe == 2 ? 1u << 14 : 0u);
+}
+
 // Launches one pass of a schedule over n_polys polynomials.
 static cudaError_t launch_pass(const hx_plan_s* plan, const PassCfg& p, uint64_t* out,
                                const uint64_t* in, uint32_t n_polys, bool forward, bool last,
@@ -131,10 +138,14 @@ static cudaError_t launch_pass(const hx_plan_s* plan, const PassCfg& p, uint64_t
         const int per_sm = resident_blocks(k, threads, smem, &sms);
         const uint64_t total = (uint64_t)tiles * n_polys * plan->n_limbs;
         const uint64_t grid = std::min<uint64_t>(total, (uint64_t)per_sm * sms);
+        const uint32_t slot = timing_begin(stream, pass_kernel_id(forward, p));
         k<<<(unsigned)grid, threads, smem, stream>>>(a);
+        timing_end(slot, stream);
     } else {
         dim3 grid(tiles * ((n_polys + p.np - 1) / p.np), plan->n_limbs);
+        const uint32_t slot = timing_begin(stream, pass_kernel_id(forward, p));
         k<<<grid, threads, smem, stream>>>(a);
+        timing_end(slot, stream);
     }
     count_launch();
     return cudaGetLastError();
@@ -218,7 +229,11 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
             t.s[i] = sc;
             t.sp[i] = (uint64_t)(((unsigned __int128)sc << 64) / q);
         }
+        const uint32_t slot = timing_begin(
+            stream, 2u | ((uint32_t)p.logR << 4) | ((uint32_t)p.K << 7) | ((uint32_t)npf << 12) |
+                        (p.pipe == 2 ? 1u << 14 : 0u));
         k<<<dim3(tiles * (npf == 3 ? 1 : 3) * n_ct, chunk), threads, smem, stream>>>(a, t);
+        timing_end(slot, stream);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

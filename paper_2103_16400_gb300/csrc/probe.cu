@@ -16,7 +16,11 @@
 // butterflies on register-resident data (no memory traffic), giving the
 // arithmetic ceiling of each Shoup-product variant of the butterfly code
 // (variants 0-2: exact quotient, lazy bound 2q; 3: truncated quotient, 4q).
+#include <stdio.h>
+
 #include <atomic>
+#include <mutex>
+#include <vector>
 
 #include "hx_internal.h"
 #include "modarith.cuh"
@@ -26,6 +30,51 @@ namespace hx {
 std::atomic<uint64_t> g_launches{0};
 
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- launch timing
+// While enabled, the NTT pass launches and the fused tensor pass record a pair
+// of CUDA events around themselves on their own stream (timing_begin before
+// the launch, timing_end after it).  The events are created when timing is
+// enabled and come back to the pool when the records are read.
+struct TimedLaunch {
+    cudaEvent_t a, b;
+    uint32_t kernel;
+};
+static std::mutex g_tm_mu;
+static bool g_tm_on = false;
+static uint32_t g_tm_cap = 0;
+static uint32_t g_tm_gen = 0;   // bumped by every read: a slot from before a read is void
+static std::vector<TimedLaunch> g_tm;
+static std::vector<cudaEvent_t> g_tm_pool;
+
+uint32_t timing_begin(cudaStream_t s, uint32_t kernel) {
+    std::lock_guard<std::mutex> g(g_tm_mu);
+    if (!g_tm_on || g_tm.size() >= g_tm_cap || g_tm_pool.size() < 2) return 0;
+    TimedLaunch t;
+    t.b = g_tm_pool.back();
+    g_tm_pool.pop_back();
+    t.a = g_tm_pool.back();
+    g_tm_pool.pop_back();
+    t.kernel = kernel;
+    if (cudaEventRecord(t.a, s) != cudaSuccess) {
+        g_tm_pool.push_back(t.a);
+        g_tm_pool.push_back(t.b);
+        return 0;
+    }
+    g_tm.push_back(t);
+    return ((g_tm_gen & 0x7ffu) << 21) | (uint32_t)g_tm.size();   // generation | index + 1
+}
+
+void timing_end(uint32_t slot, cudaStream_t s) {
+    if (!slot) return;
+    std::lock_guard<std::mutex> g(g_tm_mu);
+    const uint32_t idx = slot & ((1u << 21) - 1);
+    if ((slot >> 21) == (g_tm_gen & 0x7ffu) && idx <= g_tm.size())
+        cudaEventRecord(g_tm[idx - 1].b, s);
+}
+
+static const char* kKernelNames[3] = {"ntt_pass_kernel", "ntt_pipe_kernel",
+                                      "ntt_tensor_inv_kernel"};
 
 template <int KIND>
 __global__ void __launch_bounds__(256) int_mul_probe_kernel(uint32_t iters, uint32_t a,
@@ -156,6 +205,64 @@ static float time_probe(cudaStream_t st, F launch, uint32_t iters) {
 using namespace hx;
 
 extern "C" uint64_t hx_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" int hx_timing_enable(int on, uint32_t capacity) {
+    std::lock_guard<std::mutex> g(g_tm_mu);
+    if (!on) {
+        g_tm_on = false;
+        return HX_OK;
+    }
+    if (capacity == 0 || capacity > (1u << 20)) return HX_ERR_ARG;
+    // events for every record not yet read and every one still to come
+    const size_t want = 2 * ((size_t)capacity - std::min<size_t>(capacity, g_tm.size()));
+    while (g_tm_pool.size() < want) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return HX_ERR_CUDA;
+        g_tm_pool.push_back(e);
+    }
+    g_tm_cap = capacity;
+    g_tm_on = true;
+    return HX_OK;
+}
+
+extern "C" int hx_timing_read(hx_launch_time* h_out, uint32_t cap, uint32_t* n_out) {
+    if (!n_out || (!h_out && cap)) return HX_ERR_NULL;
+    std::lock_guard<std::mutex> g(g_tm_mu);
+    uint32_t n = 0;
+    int st = HX_OK;
+    for (const TimedLaunch& t : g_tm) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess)
+            st = HX_ERR_CUDA;
+        else if (n < cap)
+            h_out[n++] = hx_launch_time{t.kernel, 0, ms, 0.f};
+        g_tm_pool.push_back(t.a);
+        g_tm_pool.push_back(t.b);
+    }
+    g_tm.clear();
+    ++g_tm_gen;
+    *n_out = n;
+    return st;
+}
+
+extern "C" int hx_kernel_name(uint32_t kernel, char* buf, uint32_t len) {
+    if (!buf || !len) return HX_ERR_NULL;
+    const uint32_t kind = kernel & 3u, fwd = (kernel >> 2) & 1u, column = (kernel >> 3) & 1u;
+    const uint32_t logR = (kernel >> 4) & 7u, K = (kernel >> 7) & 31u;
+    const uint32_t np = (kernel >> 12) & 3u, tws = (kernel >> 14) & 1u;
+    int w;
+    if (kind == 0)
+        w = snprintf(buf, len, "%s<%u, %u, %u, %u, %u, %u>", kKernelNames[0], fwd, column, logR,
+                     K, np, tws);
+    else if (kind == 1)
+        w = snprintf(buf, len, "%s<%u, %u, %u, %u>", kKernelNames[1], fwd, column, logR, K);
+    else if (kind == 2)
+        w = snprintf(buf, len, "%s<%u, %u, %u, %u>", kKernelNames[2], logR, K, tws, np);
+    else
+        return HX_ERR_ARG;
+    return w < 0 || (uint32_t)w >= len ? HX_ERR_CAPACITY : HX_OK;
+}
 
 extern "C" int hx_probe_int_mul_rate(uint32_t kind, uint32_t iters, double* ops_per_s, float* ms,
                                      hx_stream_t stream) {
