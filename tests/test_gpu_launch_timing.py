@@ -42,8 +42,10 @@ def test_records_match_launches(hexlib):
     recs = capi.hx_timing_read(64)
     assert len(recs) == n == 8                    # 2 forward passes + fused + last inverse pass
     names = [capi.hx_kernel_name(k) for k, _ in recs]
-    assert names[:4] == ["ntt_pass_kernel<1, 1, 4, 7, 1, 0>", "ntt_pass_kernel<1, 0, 3, 7, 1, 1>",
-                         "ntt_tensor_inv_kernel<3, 7, 1, 1>", "ntt_pass_kernel<0, 1, 4, 7, 1, 0>"]
+    # passes are (s0, K, logGb, logGc, logR, pipe, np): the row pass runs two
+    # polynomials a thread, so the fused pass computes all three outputs a block
+    assert names[:4] == ["ntt_pass_kernel<1, 1, 4, 7, 1, 0>", "ntt_pass_kernel<1, 0, 3, 7, 2, 0>",
+                         "ntt_tensor_inv_kernel<3, 7, 0, 3>", "ntt_pass_kernel<0, 1, 4, 7, 1, 0>"]
     assert names[4:] == names[:4]
     assert all(ms > 0 for _, ms in recs)
     np.testing.assert_array_equal(to_host(R), ref)
