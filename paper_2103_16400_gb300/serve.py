@@ -103,7 +103,7 @@ class Server:
         self.budget = int(hbm_budget)
         self.max_batch = max_batch
         self.blocking_wait = blocking_wait
-        torch.cuda.set_device(device)
+        self._bind_device()
         capi.load()
         if isinstance(streams, int):
             streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
@@ -126,6 +126,10 @@ class Server:
         self._stop = threading.Event()
         self._threads: List[threading.Thread] = []
         self._error: Optional[BaseException] = None
+
+    def _bind_device(self):
+        """Makes the server's device current in the calling thread."""
+        self.torch.cuda.set_device(self.device)
 
     # ------------------------------------------------------------ client side
     def plan(self, N: int, moduli: Sequence[int]) -> "capi.Plan":
@@ -190,7 +194,7 @@ class Server:
         self.waiting.clear()
 
     def _run(self):
-        self.torch.cuda.set_device(self.device)
+        self._bind_device()
         try:
             while not self._stop.is_set():
                 try:
@@ -310,7 +314,7 @@ class Server:
 
     # ------------------------------------------------------------ completer
     def _complete(self):
-        self.torch.cuda.set_device(self.device)
+        self._bind_device()
         while True:
             b = self.done_q.get()
             if b is None:
