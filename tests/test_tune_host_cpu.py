@@ -1,0 +1,49 @@
+"""The autotuner's host logic (no GPU): every candidate schedule runs the
+stages 0 .. log2 N - 1 exactly once, in order, as one pass (N <= 2^13) or a
+column pass then a row pass of 6 to 13 stages each; cache keys tell apart
+the GPU, N, the width mix and the batch; the cache survives a round trip."""
+import pytest
+
+import workloads as W
+from paper_2103_16400_gb300 import tune
+
+
+@pytest.mark.parametrize("logN", range(10, 18))
+def test_candidates_cover_every_stage_once(logN):
+    cands = tune.candidates(logN)
+    assert cands
+    for sched in cands:
+        s0 = 0
+        for p in sched:
+            assert p[0] == s0                          # passes follow each other
+            s0 += p[1]
+            assert (p[4], p[5], p[6]) in tune.VARIANTS
+        assert s0 == logN
+        if len(sched) == 1:
+            assert logN <= 13 and sched[0][2] == sched[0][3] == 0
+        else:
+            col, row = sched
+            assert col[2] == 0 and col[3] in (2, 3, 4, 5)   # column tiles
+            assert row[3] == 0 and 0 <= row[2] <= 5         # row tiles
+            assert 6 <= col[1] <= 13 and 6 <= row[1] <= 13
+    assert any(len(s) == 1 for s in cands) == (logN <= 13)
+
+
+def test_cache_keys_tell_workloads_apart():
+    mixed = W.mixed_width_primes(32)
+    k = tune._key(1 << 16, mixed, 4, "GB300")
+    assert tune.width_class(mixed) == "11n21w"
+    assert len({k, tune._key(1 << 15, mixed, 4, "GB300"), tune._key(1 << 16, mixed[:31], 4, "GB300"),
+                tune._key(1 << 16, mixed, 3, "GB300"), tune._key(1 << 16, mixed, 4, "B200")}) == 5
+    # the same width mix in another order shares the entry
+    assert tune._key(1 << 16, mixed[::-1], 4, "GB300") == k
+
+
+def test_cache_round_trip(tmp_path, monkeypatch):
+    monkeypatch.setattr(tune, "CACHE_PATH", str(tmp_path / "sub" / "cache.json"))
+    assert tune.load_cache() == {}
+    entry = {"forward": [[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]], "us": 91.5}
+    tune.save_cache({"k": entry})
+    assert tune.load_cache() == {"k": entry}
+    (tmp_path / "sub" / "cache.json").write_text("{not json")
+    assert tune.load_cache() == {}                   # a damaged cache is ignored
