@@ -249,8 +249,7 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
     const uint64_t q = lc.q, qm = (uint64_t)Word<Wd, AR>::M * lc.q;
 #pragma unroll
     for (int kk = 0; kk < R; ++kk) {
-        const int k = FWD ? kk : R - 1 - kk;
-        const int s = c.s0 + P + k;
+        const int k = FWD ? kk : R - 1 - kk;   // sub-stage: stage c.s0 + P + k
         const int hb = LOG_R - 1 - k;
         if (!FWD && P == 0 && k == 0 && c.s0 == 0) {
             // stage 0 of the inverse: N^-1 folded into the last butterfly
