@@ -116,11 +116,15 @@ def kernel_slots(kid, N, moduli, n_ct=1):
     """Algorithmic IMAD slots of one launch of a timed kernel in the step:
     a pass over its K stages (four polynomials forward, three inverse), or
     the fused pass (the element-wise step plus its K inverse stages on three
-    polynomials per ciphertext pair)."""
-    kind, fwd, K = kid & 3, (kid >> 2) & 1, (kid >> 7) & 31
+    polynomials per ciphertext pair).  An inverse pass that ends the
+    transform also scales by N^-1 (Algorithm GS's final loop): folded into
+    its last stage, that is one more Shoup product per butterfly there."""
+    kind, fwd, column, K = kid & 3, (kid >> 2) & 1, (kid >> 3) & 1, (kid >> 7) & 31
     bfly = sum(N // 2 * K * slots_per_butterfly(q) for q in moduli)
     if kind == 2:
         return n_ct * (3 * bfly + sum(N * slots_per_tensor_position(q) for q in moduli))
+    if not fwd and (column or K == N.bit_length() - 1):
+        bfly += sum(N // 2 * slots_per_butterfly(q) for q in moduli)
     return (4 if fwd else 3) * n_ct * bfly
 
 

@@ -35,7 +35,10 @@ def test_pass_slots_add_up_to_the_transform(logN, K1):
     row = bench.kernel_slots(kid(0, 1, 0, 3, logN - K1), N, moduli)
     assert col + row == 4 * sum(bench.imad_slots_per_transform(N, moduli))
     inv = bench.kernel_slots(kid(0, 0, 1, 4, K1), N, moduli)
-    assert inv * 4 == col * 3                     # three polynomials in the inverse
+    # three polynomials in the inverse, whose last stage also scales by N^-1
+    scale = 3 * sum(N // 2 * bench.slots_per_butterfly(q) for q in moduli)
+    assert (inv - scale) * 4 == col * 3
+    assert bench.kernel_slots(kid(0, 0, 0, 3, logN - K1), N, moduli) * 4 == row * 3
 
 
 def test_fused_slots_are_butterflies_plus_the_tensor_step():
