@@ -347,6 +347,25 @@ int hx_batch_run_static(const hx_ragged_item* h_items, uint32_t n_items, uint32_
                         uint32_t input_mod_factor, uint32_t output_mod_factor,
                         hx_stream_t stream);
 
+/* hx_ntt_ragged: the same single run of a ragged set of transforms (Algorithm
+ * CT forward or GS inverse with N^-1, per item's plan; direction 1 or 2 and
+ * the mod factors as for hx_batch_create), with the work counters and the
+ * tile list in a caller-owned device workspace instead of the library's
+ * fixed array -- the serving primitive for transform requests: calls on
+ * different streams, each with its own workspace, may overlap.
+ *   d_workspace: device memory, 256-byte aligned, at least the size
+ *   hx_ntt_ragged_workspace reports for the same items (256 bytes plus 32
+ *   bytes per tile); reusable by calls ordered on one stream.  The tile list
+ *   is written on the host into the library's pooled page-locked staging
+ *   (as for hx_polymul_ragged) and uploaded on `stream`; two kernels run on
+ *   `stream` (one for N <= 2^11 alone).  The call returns without waiting.
+ *   Errors: those of hx_batch_create, HX_ERR_ALIGN (workspace),
+ *   HX_ERR_CAPACITY (workspace too small), HX_ERR_NOMEM (no staging). */
+int hx_ntt_ragged_workspace(const hx_ragged_item* h_items, uint32_t n_items, uint64_t* bytes);
+int hx_ntt_ragged(const hx_ragged_item* h_items, uint32_t n_items, uint32_t direction,
+                  uint32_t input_mod_factor, uint32_t output_mod_factor, void* d_workspace,
+                  uint64_t workspace_bytes, hx_stream_t stream);
+
 /* --------------------------------------------- ragged products (serving primitive)
  * hx_polymul_ragged: for every item, d_result = d_a * d_b in R_q for each
  *   polynomial and limb of the item's plan, composed as the paper's Listing 4

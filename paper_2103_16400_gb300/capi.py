@@ -60,6 +60,8 @@ _SIGS = {
                                 ctypes.POINTER(ctypes.c_float), VP],
     "hx_probe_copy_rate": [VP, VP, U64, U32, U32, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_float), VP],
+    "hx_ntt_ragged_workspace": [VP, U32, P64],
+    "hx_ntt_ragged": [VP, U32, U32, U32, U32, VP, U64, VP],
     "hx_timing_enable": [I32, U32],
     "hx_timing_read": [VP, U32, ctypes.POINTER(U32)],
     "hx_kernel_name": [U32, ctypes.c_char_p, U32],
@@ -268,6 +270,58 @@ def hx_batch_run_static(items, direction: int = 1, input_mod_factor: int = 1,
     _check("hx_batch_run_static", load().hx_batch_run_static(
         ctypes.cast(arr, VP), len(items), direction, input_mod_factor, output_mod_factor,
         _stream(stream)))
+
+
+def ragged_items_array(plans, in_ptrs, out_ptrs, n_polys=1):
+    """hx_ragged_item array built column by column in numpy (plan handles and
+    device pointers as integer sequences or arrays).  Returns (array, n)."""
+    import numpy as np
+    n = len(plans)
+    arr = np.zeros(n, _ragged_dtype())
+    arr["plan"] = plans
+    arr["d_in"] = in_ptrs
+    arr["d_out"] = out_ptrs
+    arr["n_polys"] = n_polys
+    return arr, n
+
+
+@functools.lru_cache(maxsize=None)
+def _ragged_dtype():
+    import numpy as np
+    dt = np.dtype([("plan", "<u8"), ("d_in", "<u8"), ("d_out", "<u8"), ("n_polys", "<u4"),
+                   ("reserved", "<u4")])
+    assert dt.itemsize == ctypes.sizeof(RaggedItem)
+    return dt
+
+
+def _ragged_ptr(items):
+    """(address, n) of ragged items: (plan, d_in, d_out, n_polys) tuples or a
+    ragged_items_array() pair; the returned object keeps the array alive."""
+    if isinstance(items, tuple) and len(items) == 2 and hasattr(items[0], "dtype"):
+        arr, n = items
+        if not arr.flags["C_CONTIGUOUS"] or arr.dtype != _ragged_dtype():
+            raise ValueError("item array must be a contiguous ragged_items_array()")
+        return VP(arr.ctypes.data), n, arr
+    items = list(items)
+    arr = (RaggedItem * len(items))(*[RaggedItem(_h(p), ptr(i), ptr(o), n, 0)
+                                      for p, i, o, n in items])
+    return ctypes.cast(arr, VP), len(items), arr
+
+
+def hx_ntt_ragged_workspace(items) -> int:
+    p, n, _keep = _ragged_ptr(items)
+    out = U64()
+    _check("hx_ntt_ragged_workspace", load().hx_ntt_ragged_workspace(p, n, ctypes.byref(out)))
+    return out.value
+
+
+def hx_ntt_ragged(items, workspace, workspace_bytes: int, direction: int = 1,
+                  input_mod_factor: int = 1, output_mod_factor: int = 1, stream=None):
+    """One run of a ragged set of transforms in a caller-owned workspace."""
+    p, n, _keep = _ragged_ptr(items)
+    _check("hx_ntt_ragged", load().hx_ntt_ragged(p, n, direction, input_mod_factor,
+                                                 output_mod_factor, ptr(workspace),
+                                                 workspace_bytes, _stream(stream)))
 
 
 class Batch:

@@ -321,9 +321,13 @@ static int static_scratch_address(void** out) {
 
 }  // namespace hx
 
-extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items,
-                                   uint32_t direction, uint32_t in_mf, uint32_t out_mf,
-                                   hx_stream_t stream) {
+namespace hx {
+
+// Checks a ragged set of transforms (the rules of hx_batch_create) and counts
+// its tiles: first pass (column or single) and second pass (row).
+static int rag_check_count(const hx_ragged_item* items, uint32_t n_items, uint32_t direction,
+                           uint32_t in_mf, uint32_t out_mf, uint64_t* n_first,
+                           uint64_t* n_second) {
     if (!items) return HX_ERR_NULL;
     if (n_items == 0 || (direction != 1 && direction != 2)) return HX_ERR_ARG;
     const bool fwd = direction == 1;
@@ -332,8 +336,7 @@ extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items
         return HX_ERR_MOD_FACTOR;
     int dev = 0;
     cudaGetDevice(&dev);
-    // count the tiles first, so an oversized request is refused before any work
-    uint64_t n_first = 0, n_second = 0;
+    *n_first = *n_second = 0;
     for (uint32_t i = 0; i < n_items; ++i) {
         const hx_ragged_item& it = items[i];
         if (!it.plan || !it.d_in || !it.d_out) return HX_ERR_NULL;
@@ -346,13 +349,17 @@ extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items
             return HX_ERR_OVERLAP;
         const uint64_t tiles = p->logN <= 11 ? 1u : (1u << (p->logN - 11));
         const uint64_t t = tiles * it.n_polys * p->n_limbs;
-        n_first += t;
-        if (p->logN > 11) n_second += t;
+        *n_first += t;
+        if (p->logN > 11) *n_second += t;
     }
-    if (n_first + n_second > kStaticMaxTiles) return HX_ERR_CAPACITY;
+    return HX_OK;
+}
 
-    std::vector<RagTile> tiles;   // host staging of the tile list (first pass, then second)
-    tiles.reserve(n_first + n_second);
+// Writes the tile list of a checked set: the n_first first-pass tiles, then
+// the n_second second-pass tiles.
+static void rag_fill(const hx_ragged_item* items, uint32_t n_items, bool fwd, uint32_t out_mf,
+                     RagTile* dst) {
+    uint64_t n = 0;
     for (int pass = 0; pass < 2; ++pass) {
         for (uint32_t i = 0; i < n_items; ++i) {
             const hx_ragged_item& it = items[i];
@@ -367,20 +374,54 @@ extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items
                     const uint64_t off = ((uint64_t)poly * p->n_limbs + l) << p->logN;
                     for (uint32_t t = 0; t < nt; ++t) {
                         if (pass == 0)
-                            tiles.push_back(RagTile{it.d_in + off, it.d_out + off, p->d_limbs + l, t,
-                                                    (uint8_t)first, (uint8_t)p->logN,
-                                                    (uint8_t)(k2 < 0), (uint8_t)out_mf});
+                            dst[n++] = RagTile{it.d_in + off, it.d_out + off, p->d_limbs + l, t,
+                                               (uint8_t)first, (uint8_t)p->logN,
+                                               (uint8_t)(k2 < 0), (uint8_t)out_mf};
                         else
-                            tiles.push_back(RagTile{it.d_out + off, it.d_out + off, p->d_limbs + l,
-                                                    t, (uint8_t)second, (uint8_t)p->logN, 1,
-                                                    (uint8_t)out_mf});
+                            dst[n++] = RagTile{it.d_out + off, it.d_out + off, p->d_limbs + l, t,
+                                               (uint8_t)second, (uint8_t)p->logN, 1,
+                                               (uint8_t)out_mf};
                     }
                 }
             }
         }
     }
+}
+
+// Enqueues the two persistent passes over a tile list already on the device.
+static int rag_launch(bool fwd, const RagTile* d_tiles, uint64_t n_first, uint64_t n_second,
+                      uint32_t* counters, cudaStream_t s) {
+    const int grid = rag_grid(fwd);
+    const uint64_t ns[2] = {n_first, n_second};
+    for (int p = 0; p < 2; ++p) {
+        if (!ns[p]) continue;
+        const RagTile* t = d_tiles + (p ? n_first : 0);
+        const unsigned g = (unsigned)std::min<uint64_t>(ns[p], (uint64_t)grid);
+        if (fwd)
+            ragged_pass_kernel<true><<<g, 256, kRagSmem, s>>>(t, (uint32_t)ns[p], counters + p);
+        else
+            ragged_pass_kernel<false><<<g, 256, kRagSmem, s>>>(t, (uint32_t)ns[p], counters + p);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) return HX_ERR_CUDA;
+    }
+    return HX_OK;
+}
+
+}  // namespace hx
+
+extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items,
+                                   uint32_t direction, uint32_t in_mf, uint32_t out_mf,
+                                   hx_stream_t stream) {
+    // count the tiles first, so an oversized request is refused before any work
+    uint64_t n_first = 0, n_second = 0;
+    int st = rag_check_count(items, n_items, direction, in_mf, out_mf, &n_first, &n_second);
+    if (st != HX_OK) return st;
+    if (n_first + n_second > kStaticMaxTiles) return HX_ERR_CAPACITY;
+    const bool fwd = direction == 1;
+    std::vector<RagTile> tiles(n_first + n_second);   // host staging of the tile list
+    rag_fill(items, n_items, fwd, out_mf, tiles.data());
     void* base = nullptr;
-    int st = static_scratch_address(&base);
+    st = static_scratch_address(&base);
     if (st != HX_OK) return st;
     uint32_t* counters = (uint32_t*)base;
     RagTile* d_tiles = (RagTile*)((unsigned char*)base + kStaticHeader);
@@ -390,20 +431,7 @@ extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items
     if (cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(RagTile),
                         cudaMemcpyHostToDevice, s) != cudaSuccess)
         return HX_ERR_CUDA;
-    const int grid = rag_grid(fwd);
-    const uint32_t ns[2] = {(uint32_t)n_first, (uint32_t)n_second};
-    for (int p = 0; p < 2; ++p) {
-        if (!ns[p]) continue;
-        const RagTile* t = d_tiles + (p ? n_first : 0);
-        const unsigned g = (unsigned)std::min<uint64_t>(ns[p], (uint64_t)grid);
-        if (fwd)
-            ragged_pass_kernel<true><<<g, 256, kRagSmem, s>>>(t, ns[p], counters + p);
-        else
-            ragged_pass_kernel<false><<<g, 256, kRagSmem, s>>>(t, ns[p], counters + p);
-        count_launch();
-        if (cudaGetLastError() != cudaSuccess) return HX_ERR_CUDA;
-    }
-    return HX_OK;
+    return rag_launch(fwd, d_tiles, n_first, n_second, counters, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -639,4 +667,56 @@ extern "C" int hx_polymul_ragged(const hx_polymul_item* items, uint32_t n_items,
     if (e == cudaSuccess) e = pass(false, dt + L.fA + L.fB, L.iA, counters + 2, gi);
     if (e == cudaSuccess) e = pass(false, dt + L.fA + L.fB + L.iA, L.iB, counters + 3, gi);
     return e == cudaSuccess ? HX_OK : HX_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Ragged transforms in a caller-provided workspace (the serving primitive for
+// NTT requests): the set of hx_batch_create, run once like
+// hx_batch_run_static, with the counters and the tile list in the caller's
+// workspace instead of the library's fixed array, so calls on different
+// streams, each with its own workspace, may overlap.
+// ---------------------------------------------------------------------------
+static const uint64_t kNttWsHeader = 256;   // the two work counters
+
+extern "C" int hx_ntt_ragged_workspace(const hx_ragged_item* items, uint32_t n_items,
+                                       uint64_t* bytes) {
+    if (!bytes) return HX_ERR_NULL;
+    uint64_t n_first = 0, n_second = 0;
+    int st = rag_check_count(items, n_items, 1, 1, 1, &n_first, &n_second);
+    if (st != HX_OK) return st;
+    if (n_first > 0xffffffffull || n_second > 0xffffffffull) return HX_ERR_CAPACITY;
+    const uint64_t b = kNttWsHeader + (n_first + n_second) * sizeof(RagTile);
+    *bytes = (b + 255) & ~255ull;
+    return HX_OK;
+}
+
+extern "C" int hx_ntt_ragged(const hx_ragged_item* items, uint32_t n_items, uint32_t direction,
+                             uint32_t in_mf, uint32_t out_mf, void* d_workspace,
+                             uint64_t workspace_bytes, hx_stream_t stream) {
+    if (!d_workspace) return HX_ERR_NULL;
+    if ((uintptr_t)d_workspace & 255u) return HX_ERR_ALIGN;
+    uint64_t n_first = 0, n_second = 0;
+    int st = rag_check_count(items, n_items, direction, in_mf, out_mf, &n_first, &n_second);
+    if (st != HX_OK) return st;
+    if (n_first > 0xffffffffull || n_second > 0xffffffffull) return HX_ERR_CAPACITY;
+    const uint64_t tile_bytes = (n_first + n_second) * sizeof(RagTile);
+    if (workspace_bytes < kNttWsHeader + tile_bytes) return HX_ERR_CAPACITY;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    DescStaging* stage = staging_acquire(tile_bytes, dev);
+    if (!stage) return HX_ERR_NOMEM;
+    const bool fwd = direction == 1;
+    rag_fill(items, n_items, fwd, out_mf, (RagTile*)stage->buf);
+    unsigned char* ws = (unsigned char*)d_workspace;
+    uint32_t* counters = (uint32_t*)ws;
+    RagTile* d_tiles = (RagTile*)(ws + kNttWsHeader);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool staged =
+        cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), s) == cudaSuccess &&
+        cudaMemcpyAsync(d_tiles, stage->buf, tile_bytes, cudaMemcpyHostToDevice, s) ==
+            cudaSuccess &&
+        cudaEventRecord(stage->done, s) == cudaSuccess;
+    if (!staged) return HX_ERR_CUDA;   // stays busy: an enqueued copy may still read it
+    staging_release(stage);
+    return rag_launch(fwd, d_tiles, n_first, n_second, counters, s);
 }

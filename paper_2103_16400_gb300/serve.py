@@ -1,9 +1,10 @@
-"""Continuous-batching server for negacyclic polynomial products.
+"""Continuous-batching server for negacyclic polynomial products and NTTs.
 
 A request is one product c = a * b in R_q = Z_q[X]/(X^N + 1) over an RNS
 basis (a, b: uint64 [limbs][N] residues), computed as in the paper's
 Listing 4: forward NTT of both operands with outputs left in [0, 4q),
-EltwiseMultMod with input_mod_factor 4, inverse NTT to [0, q).
+EltwiseMultMod with input_mod_factor 4, inverse NTT to [0, q) -- or one
+forward or inverse NTT of a (Algorithms CT and GS, outputs in [0, q)).
 
 The paper's polynomial layer is single-threaded and per call (Section 3);
 its integration section notes that one call is too small to offload to an
@@ -15,10 +16,12 @@ threads and no polling:
     memory (operands, one result per request, in HBM) fits the HBM budget
     and a stream slot is free -- requests that arrive while earlier batches
     are still on the GPU join the next batch (continuous batching) -- and
-    launches each admitted batch on its own CUDA stream as one ragged
-    product call (hx_polymul_ragged: five kernels for the whole batch,
-    whatever its mix of N and moduli) into a workspace taken from the torch
-    allocator, with one upload and one download for host operands;
+    launches each admitted batch on its own CUDA stream as one ragged call
+    per kind of request (hx_polymul_ragged: five kernels for all the batch's
+    products, whatever their mix of N and moduli; hx_ntt_ragged: two for
+    its forward and two for its inverse transforms) into workspaces taken
+    from the torch allocator, with one upload and one download for host
+    operands;
   * the completer thread waits on each launched batch's end event in turn
     (the wait releases the interpreter lock), completes its requests,
     stamping their latency, returns their budget and stream, and wakes the
@@ -43,16 +46,23 @@ import numpy as np
 from . import capi
 
 
+OPS = ("mul", "fwd", "inv")
+
+
 @dataclass
 class Request:
-    """a, b: uint64 [limbs][N] residues in [0, q) -- numpy arrays on the host
-    (the result comes back as a numpy array) or int64-typed CUDA tensors
-    resident in HBM (the result is a CUDA tensor view, nothing leaves the
-    device)."""
+    """One request on an RNS polynomial, uint64 [limbs][N] residues in [0, q):
+    op "mul" -- the product a * b in R_q (Listing 4); "fwd" -- the forward
+    NTT of a (Algorithm CT, bit-reversed order, output in [0, q)); "inv" --
+    the inverse NTT of a (Algorithm GS with N^-1, bit-reversed input).  a, b
+    are numpy arrays on the host (the result comes back as a numpy array) or
+    int64-typed CUDA tensors resident in HBM (the result is a CUDA tensor
+    view, nothing leaves the device); b is only read by "mul"."""
     N: int
     moduli: Tuple[int, ...]
     a: object
-    b: object
+    b: object = None
+    op: str = "mul"
     arrival: float = 0.0             # perf_counter() at submission
     done: float = 0.0
     result: object = None
@@ -68,11 +78,14 @@ class Request:
 
     @property
     def device_bytes(self) -> int:
-        """HBM the request holds while in flight: two spectra in the batch
-        workspace and the result, plus the staged operands when they come
-        from the host (tile lists add 32 bytes per 2048 coefficients)."""
+        """HBM the request holds while in flight: for a product two spectra
+        in the batch workspace and the result, for a transform the result,
+        plus the staged operands when they come from the host and the tile
+        lists (32 bytes per tile of 2048 coefficients per pass)."""
         words = self.limbs * self.N
-        return (3 + (0 if self.resident else 2)) * words * 8 + (3 * words // 2048 + 4) * 64
+        if self.op == "mul":
+            return (3 + (0 if self.resident else 2)) * words * 8 + (3 * words // 2048 + 4) * 64
+        return (1 + (0 if self.resident else 1)) * words * 8 + (2 * words // 2048 + 2) * 32
 
     @property
     def latency(self) -> float:
@@ -142,6 +155,10 @@ class Server:
     def submit(self, req: Request, arrival: Optional[float] = None) -> Future:
         """Queue a request; its latency counts from `arrival` (a perf_counter()
         time, e.g. when a load generator scheduled it) or from now."""
+        if req.op not in OPS:
+            raise ValueError(f"unknown op {req.op!r}; expected one of {OPS}")
+        if req.op == "mul" and req.b is None:
+            raise ValueError("a product needs both operands")
         if req.device_bytes > self.budget:
             raise BudgetError(f"request needs {req.device_bytes} bytes, budget {self.budget}")
         if type(req.moduli) is not tuple:
@@ -267,23 +284,27 @@ class Server:
         host_reqs = [k for k, r in enumerate(reqs) if not r.resident]
         with torch.cuda.stream(stream):
             res = torch.empty(int(res_off[-1]), dtype=torch.int64, device=dev_name)
+            res_ptr = res.data_ptr() + 8 * res_off[:-1]
             staged = pinned = None
             a_ptr = [0] * n
             b_ptr = [0] * n
             if host_reqs:
                 # all host operands through one pinned buffer and one upload
-                total = 2 * int(sizes[host_reqs].sum())
+                n_ops = [2 if reqs[k].op == "mul" else 1 for k in host_reqs]
+                total = int(sum(int(sizes[k]) * m for k, m in zip(host_reqs, n_ops)))
                 pinned = torch.empty(total, dtype=torch.int64, pin_memory=True)
                 pv = pinned.numpy().view(np.uint64)
                 staged = torch.empty(total, dtype=torch.int64, device=dev_name)
                 base = staged.data_ptr()
                 o = 0
-                for k in host_reqs:
+                for k, m in zip(host_reqs, n_ops):
                     r, sz = reqs[k], int(sizes[k])
                     pv[o:o + sz] = r.a.reshape(-1)
-                    pv[o + sz:o + 2 * sz] = r.b.reshape(-1)
-                    a_ptr[k], b_ptr[k] = base + 8 * o, base + 8 * (o + sz)
-                    o += 2 * sz
+                    a_ptr[k] = base + 8 * o
+                    if m == 2:
+                        pv[o + sz:o + 2 * sz] = r.b.reshape(-1)
+                        b_ptr[k] = base + 8 * (o + sz)
+                    o += m * sz
                 staged.copy_(pinned, non_blocking=True)
             plans = self.plans
             handles = []
@@ -291,13 +312,32 @@ class Server:
                 p = plans.get((r.N, r.moduli))
                 handles.append((p if p is not None else self.plan(r.N, r.moduli)).handle)
                 if r.resident:
-                    a_ptr[k], b_ptr[k] = r.a.data_ptr(), r.b.data_ptr()
-            # results back to back in `res`; operands read in place
-            arr = capi.polymul_items_array(handles, a_ptr, b_ptr,
-                                           res.data_ptr() + 8 * res_off[:-1])
-            wsb = capi.hx_polymul_ragged_workspace(arr)
-            ws = torch.empty(wsb, dtype=torch.uint8, device=dev_name)
-            capi.hx_polymul_ragged(arr, ws, wsb, stream.cuda_stream)
+                    a_ptr[k] = r.a.data_ptr()
+                    if r.op == "mul":
+                        b_ptr[k] = r.b.data_ptr()
+            # one ragged call per kind of request, each into its own workspace;
+            # results back to back in `res`, operands read in place
+            workspaces = []
+            for op in OPS:
+                idx = [k for k, r in enumerate(reqs) if r.op == op]
+                if not idx:
+                    continue
+                h = [handles[k] for k in idx]
+                if op == "mul":
+                    arr = capi.polymul_items_array(h, [a_ptr[k] for k in idx],
+                                                   [b_ptr[k] for k in idx], res_ptr[idx])
+                    wsb = capi.hx_polymul_ragged_workspace(arr)
+                    ws = torch.empty(wsb, dtype=torch.uint8, device=dev_name)
+                    capi.hx_polymul_ragged(arr, ws, wsb, stream.cuda_stream)
+                    self._count_launches(5)
+                else:
+                    arr = capi.ragged_items_array(h, [a_ptr[k] for k in idx], res_ptr[idx])
+                    wsb = capi.hx_ntt_ragged_workspace(arr)
+                    ws = torch.empty(wsb, dtype=torch.uint8, device=dev_name)
+                    capi.hx_ntt_ragged(arr, ws, wsb, 1 if op == "fwd" else 2, 1, 1,
+                                       stream.cuda_stream)
+                    self._count_launches(2)
+                workspaces.append(ws)
             out_host = None
             if host_reqs:
                 out_host = torch.empty(int(res_off[-1]), dtype=torch.int64, pin_memory=True)
@@ -307,10 +347,13 @@ class Server:
         with self._lock:
             self.stats["batches"] += 1
             self.stats["requests"] += n
-            self.stats["launches"] += 5
             self.stats["max_batch"] = max(self.stats["max_batch"], n)
-        work = (res, sizes, out_host, staged, pinned, ws)
+        work = (res, sizes, out_host, staged, pinned, workspaces)
         return {"reqs": reqs, "work": work, "event": ev, "sid": sid, "bytes": need}
+
+    def _count_launches(self, k: int):
+        with self._lock:
+            self.stats["launches"] += k
 
     # ------------------------------------------------------------ completer
     def _complete(self):
@@ -353,7 +396,8 @@ class Server:
 def serve_one_by_one(reqs: Sequence[Request], arrivals: Optional[Sequence[float]] = None,
                      plans: Optional[dict] = None, device: int = 0) -> None:
     """The unbatched baseline: each request alone, in arrival order, with the
-    plain per-request calls (upload, hx_poly_mul, download, wait).  When
+    plain per-request calls (upload, hx_poly_mul or hx_ntt_forward /
+    hx_ntt_inverse, download, wait).  When
     `arrivals` (offsets in seconds) are given, a request does not start
     before its arrival time; latency counts from arrival."""
     import torch
@@ -373,12 +417,20 @@ def serve_one_by_one(reqs: Sequence[Request], arrivals: Optional[Sequence[float]
         key = (r.N, tuple(r.moduli))
         if key not in plans:
             plans[key] = capi.Plan(r.N, key[1])
-        if r.resident:
-            a, b = r.a.clone(), r.b.clone()         # hx_poly_mul overwrites its operands
+        dev = f"cuda:{device}"
+        if r.op == "mul":
+            if r.resident:
+                a, b = r.a.clone(), r.b.clone()     # hx_poly_mul overwrites its operands
+            else:
+                a = torch.from_numpy(r.a.view(np.int64)).to(dev, non_blocking=True)
+                b = torch.from_numpy(r.b.view(np.int64)).to(dev, non_blocking=True)
+            capi.hx_poly_mul(plans[key], a, a, b, 1, stream.cuda_stream)
         else:
-            a = torch.from_numpy(r.a.view(np.int64)).to(f"cuda:{device}", non_blocking=True)
-            b = torch.from_numpy(r.b.view(np.int64)).to(f"cuda:{device}", non_blocking=True)
-        capi.hx_poly_mul(plans[key], a, a, b, 1, stream.cuda_stream)
+            x = r.a if r.resident else torch.from_numpy(r.a.view(np.int64)).to(
+                dev, non_blocking=True)
+            a = torch.empty_like(x)
+            (capi.hx_ntt_forward if r.op == "fwd" else capi.hx_ntt_inverse)(
+                plans[key], a, x, 1, 1, 1, stream.cuda_stream)
         if r.resident:
             stream.synchronize()
             r.result = a

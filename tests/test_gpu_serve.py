@@ -29,7 +29,7 @@ def make_requests(n, seed, max_limbs=6):
 
 
 def clone(reqs):
-    return [serve.Request(r.N, r.moduli, r.a, r.b) for r in reqs]
+    return [serve.Request(r.N, r.moduli, r.a, r.b, op=r.op) for r in reqs]
 
 
 def test_results_identical_alone_and_in_the_mix(hexlib):
@@ -151,3 +151,32 @@ def test_launch_failure_fails_its_requests_and_stops_the_server(hexlib, monkeypa
     with pytest.raises(capi.HexError):
         srv.stop()
     assert srv.in_use == 0 and srv.n_inflight == 0
+
+
+def test_products_and_transforms_in_one_stream_of_requests(hexlib):
+    """Forward and inverse NTT requests mixed with products, host and
+    HBM-resident operands: every result equals the one-by-one baseline's
+    and the oracle's."""
+    from paper_2103_16400_gb300.tensors import to_device, to_host
+    reqs = make_requests(24, W.SEED_BASE + 17)
+    for k, r in enumerate(reqs):
+        r.op = ("mul", "fwd", "inv")[k % 3]
+    resident = [serve.Request(r.N, r.moduli, to_device(r.a), op=op)
+                for r, op in zip(reqs[:4], ("fwd", "inv", "fwd", "inv"))]
+    with serve.Server(hbm_budget=8 << 30, streams=3) as srv:
+        futs = [srv.submit(r) for r in clone(reqs) + resident]
+        got = [f.result(timeout=120) for f in futs]
+    base = clone(reqs)
+    serve.serve_one_by_one(base)
+    for r, g, b in zip(reqs, got, base):
+        np.testing.assert_array_equal(g, b.result)
+        if r.op == "fwd":
+            exp = oracle.ntt_forward(r.a[None], r.moduli)[0]
+        elif r.op == "inv":
+            exp = oracle.ntt_inverse(r.a[None], r.moduli)[0]
+        else:
+            exp = oracle.poly_mul(r.a[None], r.b[None], r.moduli)[0]
+        np.testing.assert_array_equal(g, exp)
+    for r, g, src in zip(resident, got[len(reqs):], reqs[:4]):
+        f = oracle.ntt_forward if r.op == "fwd" else oracle.ntt_inverse
+        np.testing.assert_array_equal(to_host(g), f(src.a[None], src.moduli)[0])

@@ -28,3 +28,16 @@ def test_malformed_item_arrays_are_refused():
         capi._items_ptr(arr[::2])                      # not contiguous
     with pytest.raises(ValueError):
         capi._items_ptr(np.zeros(2, np.uint64))        # not an item array
+
+
+def test_numpy_ragged_items_match_ctypes_items():
+    plans = [0x7f0000001000, 0x7f0000002000]
+    i = [0x7e0000000000, 0x7e0000010000]
+    o = np.array([0x7c0000000000, 0x7c0000100000], np.int64)
+    arr, n = capi.ragged_items_array(plans, i, o, [1, 3])
+    p, n2, keep = capi._ragged_ptr((arr, n))
+    assert n == n2 == 2 and p.value == arr.ctypes.data and keep is arr
+    p_ref, n_ref, ref = capi._ragged_ptr(list(zip(plans, i, [int(x) for x in o], [1, 3])))
+    assert n_ref == 2 and arr.tobytes() == bytes(ref)
+    with pytest.raises(ValueError):
+        capi._ragged_ptr((np.zeros(2, np.uint64), 2))

@@ -117,3 +117,29 @@ def test_failed_launch_fails_requests_and_stops():
     with pytest.raises(capi.HexError):
         srv.stop()
     assert srv.in_use == 0 and srv.n_inflight == 0
+
+
+def test_transform_requests_are_checked_and_sized():
+    srv = FakeServer(budget=1 << 30, n_streams=1)
+    a = np.zeros((2, 1 << 10), np.uint64)
+    with pytest.raises(ValueError):
+        srv.submit(serve.Request(1 << 10, (1, 2), a, a, op="square"))
+    with pytest.raises(ValueError):
+        srv.submit(serve.Request(1 << 10, (1, 2), a, op="mul"))      # no second operand
+    fwd = serve.Request(1 << 10, (1, 2), a, op="fwd")
+    mul = serve.Request(1 << 10, (1, 2), a, a)
+    # a transform holds its result and its staged operand; a product two
+    # spectra, its result and two staged operands
+    assert fwd.device_bytes < mul.device_bytes / 2
+
+
+def test_mixed_ops_keep_fifo_order():
+    srv = FakeServer(budget=1 << 30, n_streams=2).start()
+    reqs = [request(t) for t in range(12)]
+    for r, op in zip(reqs, ["mul", "fwd", "inv"] * 4):
+        r.op = op
+    futs = [srv.submit(r) for r in reqs]
+    for t, f in enumerate(futs):
+        assert (f.result(timeout=10) == t).all()
+    srv.stop()
+    assert [t for b in srv.batches for t in b] == list(range(12))
