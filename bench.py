@@ -945,13 +945,20 @@ def main():
                       "how": "CUDA events around each call inside the timed region"},
             "gpu_launches": launches,
             "clocks": clocks.summary()}
-    # the batched and serving reports run on rank 0 only; the other ranks wait
+    # the secondary reports run on rank 0 only; the other ranks wait.  A
+    # report that fails records its error instead of taking the line with it
+    def report(key, fn):
+        try:
+            line[key] = fn(torch)
+        except Exception as e:               # noqa: BLE001 -- reported, not hidden
+            line[key] = {"error": f"{type(e).__name__}: {e}"}
+
     if rank == 0:
-        line["eltwise"] = eltwise_report(torch)
+        report("eltwise", eltwise_report)
     if rank == 0 and not args.no_ragged:
-        line["batched"] = ragged_report(torch)
+        report("batched", ragged_report)
     if rank == 0 and not args.no_serving:
-        line["serving"] = serving_report(torch)
+        report("serving", serving_report)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(N, wl.moduli, s, sets)
     if rank == 0:
