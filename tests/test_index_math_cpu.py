@@ -239,3 +239,29 @@ def test_transform_with_these_maps_equals_the_oracle(L, split):
                             x[xi], x[yi] = (a + b) % q, (a - b) % q
     exp = oracle.ntt_forward_1(W.poly_batch(W.SEED_BASE + 990, 0, 1, [q], N)[0, 0], q)
     np.testing.assert_array_equal(np.array(x, dtype=np.uint64), exp)
+
+
+# The ragged kernels' fixed menu (2048-element tiles; 1024 for N = 2^10):
+# log2 N -> (first pass K, column?), (second pass K) as rag_kinds() picks them.
+RAG_KINDS = {10: ((10, False), None), 11: ((11, False), None), 12: ((5, True), 7),
+             13: ((6, True), 7), 14: ((7, True), 7), 15: ((7, True), 8), 16: ((8, True), 8),
+             17: ((8, True), 9)}
+
+
+def rag_pass(L, K, column):
+    """rag_tile's geometry for a menu entry (S10 runs 4 elements a thread)."""
+    s0 = 0 if column or K >= L else L - K
+    logGc = 11 - K if column else 0
+    logGb = 0 if column else (0 if K >= L else 11 - K)
+    return Pass(L, s0, K, logGb, logGc, 2 if K == 10 else 3)
+
+
+@pytest.mark.parametrize("L", range(10, 18))
+def test_ragged_menu_passes(L):
+    (K1, column), K2 = RAG_KINDS[L]
+    passes = [rag_pass(L, K1, column)] + ([rag_pass(L, K2, False)] if K2 else [])
+    assert sum(p.K for p in passes) == L
+    for p in passes:
+        assert p.logTE == min(L, 11) and p.T == 256     # 256 threads, 2048 elements (1024 at 2^10)
+        test_tiles_cover_the_transform_once(p)
+        test_rounds_registers_butterflies_and_twiddles(p)
