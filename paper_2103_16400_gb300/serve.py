@@ -101,7 +101,8 @@ _WAKE = object()   # queue token: re-check admission, nothing submitted
 
 class Server:
     """Engine and completer threads + streams; `submit()` is thread-safe and
-    returns a Future that resolves to the product (uint64 [limbs][N])."""
+    returns a Future that resolves to the request's result (the product or
+    the transform, uint64 [limbs][N])."""
 
     def __init__(self, hbm_budget: int = 64 << 30, streams=3,
                  max_batch: int = 256, device: int = 0, blocking_wait: bool = True):
