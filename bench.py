@@ -265,6 +265,55 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
+def ntt_rates_report(torch, step, dev_sets, imad_rate, iters=200):
+    """The plain transforms of the step's plan timed on their own: the forward
+    call (four polynomials, the step's inputs rotating over the input sets)
+    and the inverse call (three polynomials from the addend sets, rotating --
+    values in [0, q)), CUDA events on the launching stream; their
+    limb-transform rates, forward + inverse, and the forward + inverse
+    roofline fraction (the inverse's slots include the N^-1 scaling).  Then
+    the same step with L2 warm: one input set, no rotation."""
+    from paper_2103_16400_gb300 import capi
+    from paper_2103_16400_gb300.tensors import empty
+    N, moduli, st = step.N, step.moduli, step.stream
+    nl = len(moduli)
+    R = empty((3, nl, N))
+    out = empty((4, nl, N))
+
+    def timed(fn):
+        for i in range(3):
+            fn(i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for i in range(iters):
+            fn(i)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / iters * 1e3          # us per call
+
+    fwd_us = timed(lambda i: capi.hx_ntt_forward(step.plan, out, dev_sets[i % len(dev_sets)][0],
+                                                 4, 1, 1, st))
+    inv_us = timed(lambda i: capi.hx_ntt_inverse(step.plan, R, dev_sets[i % len(dev_sets)][1],
+                                                 3, 1, 1, st))
+    warm_ms = timed(lambda i: step.run(0)) / 1e3
+    slots_f = sum(imad_slots_per_transform(N, moduli))
+    slots_i = slots_f + sum(N // 2 * slots_per_butterfly(q) for q in moduli)   # + N^-1
+    t_f, t_i = fwd_us / (4 * nl), inv_us / (3 * nl)       # us per limb-transform
+    return {"forward_us": fwd_us, "inverse_us": inv_us,
+            "forward_limb_transforms_per_s": 1e6 / t_f,
+            "inverse_limb_transforms_per_s": 1e6 / t_i,
+            "fwd_plus_inv_pairs_per_s": 1e6 / (t_f + t_i),
+            "roofline_fwd_plus_inv_frac": (slots_f + slots_i) / ((t_f + t_i) * 1e-6) / imad_rate,
+            "schedules": {"forward": step.plan.schedule(step.plan.FORWARD),
+                          "inverse": step.plan.schedule(step.plan.INVERSE)},
+            "l2_warm_step": {"ms_per_step": warm_ms,
+                             "limb_transforms_per_s": 7 * nl / (warm_ms * 1e-3),
+                             "how": "the timed step on one input set, no rotation"},
+            "how": f"{iters} calls each, CUDA events, inputs rotating over "
+                   f"{len(dev_sets)} sets (> L2)"}
+
+
 def eltwise_report(torch, N=1 << 16, nl=32, P=4, reps=20):
     """The element-wise kernels on 4 polynomials x 32 limbs x 65536 (64 MiB
     an operand; two rotating operand sets exceed L2): algorithmic HBM bytes
@@ -954,6 +1003,7 @@ def main():
             line[key] = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
+        report("ntt_rates", lambda t: ntt_rates_report(t, step, dev_sets, imad_rate))
         report("eltwise", eltwise_report)
     if rank == 0 and not args.no_ragged:
         report("batched", ragged_report)
