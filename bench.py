@@ -875,8 +875,8 @@ def main():
     per_step_units = 7 * nl
     value = per_step_units * args.steps * ws / (total_ms / 1e3)
 
-    # roofline of the dominant kernel: the forward NTT call (4 polynomials,
-    # two pass launches), IMAD-bound; peak = mad.lo issue rate probed live
+    # roofline of the forward NTT call (4 polynomials, two pass launches; kept
+    # as roofline_forward_call), IMAD-bound; peak = mad.lo issue rate probed live
     imad_rate, _ = capi.hx_probe_int_mul_rate("mad.lo", 8192)
     fwd_call_ms = float(np.mean(fwd_ms))
     alg_slots = 4 * sum(imad_slots_per_transform(N, wl.moduli))
@@ -899,7 +899,7 @@ def main():
                               for k, v in getattr(step, "tuned", {}).items()}}
 
     # every kernel of the step timed live (library events around each launch
-    # inside the timed region); the roofline object is the dominant kernel's
+    # in the kernel-timing region); the roofline object is the dominant kernel's
     kernels = {}
     for kid, ms in timed:
         k = kernels.setdefault(kid, {"kernel": capi.hx_kernel_name(kid), "launches": 0,
