@@ -133,9 +133,16 @@ int hx_plan_info(hx_plan_t plan, uint64_t* N, uint32_t* n_limbs, uint64_t* devic
  * copies the tile's twiddle pairs into shared memory (pipe = 0: per-tile,
  * twiddles read through the read-only cache); np (1 or 2) is the number of
  * polynomials each thread transforms with one set of twiddle registers.
+ * pipe = 3 on both passes of a two-pass schedule,
+ *   {0, K1, 0, logGc, logR, 3, 1}, {K1, K2, logGb, 0, logR, 3, 1}
+ * with K2 - logGc = K1 - logGb = c in [1, 4], fuses them into one launch of
+ * thread-block clusters of 2^c CTAs per limb-transform: each CTA keeps N/2^c
+ * coefficients in shared memory, the column stages and the row stages run
+ * there, and the CTAs exchange between the two through distributed shared
+ * memory, so every coefficient crosses HBM once each way (N in [2^14, 2^17]).
  * hx_plan_set_schedule returns HX_ERR_ARG for a schedule the library cannot
  * run (stages not covering [0, log2 N), a kernel not in the menu, tile too
- * large).  `direction` selects the forward (1) or inverse (2) transform's
+ * large, a cluster shape the device cannot make resident).  `direction` selects the forward (1) or inverse (2) transform's
  * schedule, or both (3, set only); the inverse runs the same passes in
  * reverse order.  hx_plan_get_schedule writes 14 int32 (the unused second
  * pass zeroed). */

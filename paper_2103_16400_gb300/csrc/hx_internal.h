@@ -83,8 +83,10 @@ void count_launch(uint64_t n = 1);
 // probe.cu: per-launch timing (hx_timing_enable); timing_begin returns 0 when
 // off or full, else a slot to pass to timing_end after the launch.  Kernel
 // ids: bits 0-1 kind (0 per-tile pass, 1 persistent pass, 2 fused tensor
-// pass), 2 forward, 3 column, 4-6 logR, 7-11 K, 12-13 polynomials (outputs
-// for the fused pass) per block, 14 staged twiddles.
+// pass, 3 cluster-fused transform), 2 forward, 3 column, 4-6 logR, 7-11 K
+// (K1 for kind 3), 12-13 polynomials (outputs for the fused pass; for kind 3
+// bit 12 marks the tensor-fused inverse) per block, 14 staged twiddles,
+// 15-19 K2 (kind 3).
 uint32_t timing_begin(cudaStream_t s, uint32_t kernel);
 void timing_end(uint32_t slot, cudaStream_t s);
 

@@ -12,11 +12,156 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 
+#include "ntt_cluster.cuh"
 #include "ntt_kernels.cuh"
 #include "ntt_tensor.h"
 
 namespace hx {
+
+// ---------------------------------------------------------------------------
+// Cluster-fused schedules (ntt_cluster.cuh): two passes, both with pipe 3,
+//   {0, K1, 0, logGc, logR, 3, 1}, {K1, K2, logGb, 0, logR, 3, 1},
+// run as ONE launch of clusters of 2^LOG_C CTAs, LOG_C = K2 - logGc =
+// K1 - logGb: the first pass's tile is a CTA's column-phase tile, the
+// second's its row-phase tile, both N / 2^LOG_C elements.
+struct ClusterShape {
+    int K1, K2, logR, logC, logGc;
+    uint32_t threads;
+    size_t smem;
+};
+
+static bool is_cluster(const NttCfg& c) {
+    return c.npass == 2 && (c.pass[0].pipe == 3 || c.pass[1].pipe == 3);
+}
+
+// The kernel's shared-memory allowance is set at every launch: one kernel
+// serves several cluster sizes, each with its own tile size.
+static cudaError_t cluster_attrs(const void* k, const ClusterShape& s) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)s.smem);
+    if (e == cudaSuccess && s.logC > 3)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+// Whether clusters of this shape can be resident at all on the current
+// device (shared memory and registers per SM, cluster size); cached.
+static bool cluster_fits(const void* k, const ClusterShape& s) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, size_t>, bool> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(k, dev, s.logC, s.smem);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    bool ok = cluster_attrs(k, s) == cudaSuccess;
+    if (ok) {
+        cudaLaunchConfig_t lc = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1u << s.logC;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.gridDim = dim3(1u << s.logC, 1, 1);
+        lc.blockDim = dim3(s.threads, 1, 1);
+        lc.dynamicSmemBytes = s.smem;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        int n = 0;
+        ok = cudaOccupancyMaxActiveClusters(&n, k, &lc) == cudaSuccess && n > 0;
+    }
+    cudaGetLastError();   // a refused query leaves no error behind
+    cache[key] = ok;
+    return ok;
+}
+
+// Shape of a cluster-fused schedule; false if `c` is not one the library can
+// run (kind: 0 forward, 1 inverse, 2 tensor-fused inverse).
+static bool cluster_shape(int L, const NttCfg& c, int kind, ClusterShape* out) {
+    if (c.npass != 2) return false;
+    const PassCfg& a = c.pass[0];
+    const PassCfg& b = c.pass[1];
+    if (a.pipe != 3 || b.pipe != 3 || a.np != 1 || b.np != 1 || a.logR != b.logR) return false;
+    if (a.s0 != 0 || a.logGb != 0 || b.s0 != a.K || b.logGc != 0 || a.K + b.K != L) return false;
+    ClusterShape s;
+    s.K1 = a.K;
+    s.K2 = b.K;
+    s.logR = a.logR;
+    s.logGc = a.logGc;
+    s.logC = b.K - a.logGc;
+    if (s.logC != a.K - b.logGb || s.logC < 1 || s.logC > 4) return false;
+    if (a.logGc < 2 || b.logGb < 0) return false;   // >= 32-byte column segments in HBM
+    const int logE = L - s.logC, logT = logE - s.logR;
+    if (logT < 5 || logT > 10) return false;         // 32 .. 1024 threads
+    s.threads = 1u << logT;
+    s.smem = (size_t)8 * padded(1u << logE);
+    if (s.smem > 200 * 1024) return false;
+    const void* k = kind == 0   ? (const void*)pick_cluster_f(s.logR, s.K1, s.K2)
+                    : kind == 1 ? (const void*)pick_cluster_i(s.logR, s.K1, s.K2)
+                                : (const void*)pick_cluster_t(s.logR, s.K1, s.K2);
+    if (!k || !cluster_fits(k, s)) return false;
+    if (out) *out = s;
+    return true;
+}
+
+static cudaLaunchConfig_t cluster_launch_cfg(const ClusterShape& s, dim3 grid, cudaStream_t st,
+                                             cudaLaunchAttribute* at) {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1u << s.logC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = dim3(s.threads, 1, 1);
+    lc.dynamicSmemBytes = s.smem;
+    lc.stream = st;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return lc;
+}
+
+// Kernel id of a cluster launch for launch timing: kind 3, bit 2 forward,
+// bits 4-6 logR, 7-11 K1, bit 12 tensor-fused, 15-19 K2.
+static uint32_t cluster_kernel_id(bool fwd, bool tensor, const ClusterShape& s) {
+    return 3u | (fwd ? 4u : 0u) | ((uint32_t)s.logR << 4) | ((uint32_t)s.K1 << 7) |
+           (tensor ? 1u << 12 : 0u) | ((uint32_t)s.K2 << 15);
+}
+
+static cudaError_t launch_cluster(const hx_plan_s* plan, const NttCfg& cfg, uint64_t* out,
+                                  const uint64_t* in, uint32_t n_polys, bool forward,
+                                  uint32_t out_mf, cudaStream_t stream) {
+    ClusterShape s;
+    if (!cluster_shape(plan->logN, cfg, forward ? 0 : 1, &s)) return cudaErrorInvalidConfiguration;
+    PassArgs a{};
+    a.out = out;
+    a.in = in;
+    a.limbs = plan->d_limbs;
+    a.order = plan->d_order;   // few long blocks: the costliest limbs start first
+    a.n_limbs = plan->n_limbs;
+    a.n_polys = n_polys;
+    a.L = plan->logN;
+    a.s0 = 0;
+    a.logGb = s.K1 - s.logC;
+    a.logGc = s.logGc;
+    a.log_tiles_c = 0;
+    a.last = 1;
+    a.out_mf = out_mf;
+    ClusterKernel k = forward ? pick_cluster_f(s.logR, s.K1, s.K2)
+                              : pick_cluster_i(s.logR, s.K1, s.K2);
+    cudaError_t e = cluster_attrs((const void*)k, s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t lc =
+        cluster_launch_cfg(s, dim3(n_polys << s.logC, plan->n_limbs, 1), stream, at);
+    const uint32_t slot = timing_begin(stream, cluster_kernel_id(forward, false, s));
+    e = cudaLaunchKernelEx(&lc, k, a);
+    timing_end(slot, stream);
+    count_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 static PassKernel pick(bool fwd, const PassCfg& p) {
     const bool column = p.logGc > 0;
@@ -65,6 +210,8 @@ static bool pass_ok(int L, const PassCfg& p) {
 }
 
 bool cfg_supported(int L, const NttCfg& cfg) {
+    if (is_cluster(cfg))
+        return cluster_shape(L, cfg, 0, nullptr) && cluster_shape(L, cfg, 1, nullptr);
     if (cfg.npass < 1 || cfg.npass > 2) return false;
     int s = 0;
     for (int i = 0; i < cfg.npass; ++i) {
@@ -155,6 +302,8 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
                        uint32_t n_polys, bool forward, uint32_t in_mf, uint32_t out_mf,
                        const NttCfg& cfg, cudaStream_t stream) {
     (void)in_mf;  // every allowed input range is inside the butterflies' lazy range
+    if (is_cluster(cfg))
+        return launch_cluster(plan, cfg, out, in, n_polys, forward, out_mf, stream);
     for (int step = 0; step < cfg.npass; ++step) {
         const int pi = forward ? step : cfg.npass - 1 - step;
         cudaError_t e = launch_pass(plan, cfg.pass[pi], out, step == 0 ? in : out, n_polys,
@@ -173,7 +322,60 @@ static int tensor_npf(const PassCfg& p) { return p.np > 1 ? 3 : 1; }
 // the fused pass's launches maps onto itself.
 static_assert(kTensorLimbs == 64, "launch_order permutes within runs of kTensorLimbs");
 
+// One cluster-fused launch per 64 limbs: the tensor's element-wise step in
+// the inverse's first (row) phase, then the whole inverse transform.
+static cudaError_t launch_cluster_tensor(const hx_plan_s* plan, uint64_t* out, const uint64_t* A,
+                                         const uint64_t* E, uint32_t n_ct,
+                                         const uint64_t* h_scalars, uint32_t in_mf,
+                                         const NttCfg& cfg, cudaStream_t stream) {
+    ClusterShape s;
+    if (!cluster_shape(plan->logN, cfg, 2, &s)) return cudaErrorInvalidConfiguration;
+    PassArgs a{};
+    a.out = out;
+    a.in = nullptr;
+    a.limbs = plan->d_limbs;
+    a.order = plan->d_order;
+    a.n_limbs = plan->n_limbs;
+    a.n_polys = 3 * n_ct;
+    a.L = plan->logN;
+    a.logGb = s.K1 - s.logC;
+    a.logGc = s.logGc;
+    a.last = 1;
+    a.out_mf = 1;
+    ClusterTensorKernel k = pick_cluster_t(s.logR, s.K1, s.K2);
+    const cudaError_t ea = cluster_attrs((const void*)k, s);
+    if (ea != cudaSuccess) return ea;
+    for (uint32_t limb0 = 0; limb0 < plan->n_limbs; limb0 += kTensorLimbs) {
+        const uint32_t chunk = std::min<uint32_t>(kTensorLimbs, plan->n_limbs - limb0);
+        TensorIn t{};
+        t.A = A;
+        t.E = E;
+        t.n_ct = n_ct;
+        t.in_mf = in_mf;
+        t.limb0 = limb0;
+        for (uint32_t i = 0; i < chunk; ++i) {
+            const uint64_t q = plan->moduli[limb0 + i], sc = h_scalars[limb0 + i];
+            t.s[i] = sc;
+            t.sp[i] = (uint64_t)(((unsigned __int128)sc << 64) / q);
+        }
+        cudaLaunchAttribute at[1];
+        const cudaLaunchConfig_t lc =
+            cluster_launch_cfg(s, dim3((3 * n_ct) << s.logC, chunk, 1), stream, at);
+        const uint32_t slot = timing_begin(stream, cluster_kernel_id(false, true, s));
+        cudaError_t e = cudaLaunchKernelEx(&lc, k, a, t);
+        timing_end(slot, stream);
+        count_launch();
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 bool tensor_fusable(const NttCfg& cfg) {
+    if (is_cluster(cfg)) {
+        const int L = cfg.pass[0].K + cfg.pass[1].K;
+        return cluster_shape(L, cfg, 2, nullptr);
+    }
     const PassCfg& p = cfg.pass[cfg.npass - 1];   // the inverse runs this pass first
     if (p.pipe == 1 || p.logGc != 0) return false;
     if (!pick_tensor_inv(p.logR, p.K, p.pipe == 2, tensor_npf(p))) return false;
@@ -187,6 +389,8 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
                                   const uint64_t* E, uint32_t n_ct, const uint64_t* h_scalars,
                                   uint32_t in_mf, const NttCfg& cfg, cudaStream_t stream) {
     if (!tensor_fusable(cfg)) return cudaErrorNotSupported;
+    if (is_cluster(cfg))
+        return launch_cluster_tensor(plan, out, A, E, n_ct, h_scalars, in_mf, cfg, stream);
     const int L = plan->logN;
     const PassCfg& p = cfg.pass[cfg.npass - 1];
     const int npf = tensor_npf(p);

@@ -157,6 +157,12 @@ struct TileCtx {
     bool last;
     uint64_t poly_stride = 0;   // elements between the same limb of consecutive polynomials
     uint32_t np_valid = 1;      // polynomials of this block's group that exist
+    // Cluster-fused transforms (ntt_cluster.cuh): the round that reads its
+    // elements from the other phase's layout in the cluster's shared memory.
+    uint32_t xsm = 0;      // shared-window address of this CTA's data tile
+    int xK2 = 0;           // row-phase stages (log2 of a row's length)
+    int xlogGc = 0;        // log2 of the columns each CTA holds in the column phase
+    int xlogGb = 0;        // log2 of the rows each CTA holds in the row phase
 };
 
 // Global index of local tile element l = (bl, e, cl).  Row passes (ROW: the
@@ -172,7 +178,56 @@ __device__ __forceinline__ uint64_t tile_gidx(uint32_t l, const TileCtx& t) {
     return ((t.b_base + bl) << (t.L - t.s0)) + (e << t.w) + t.c_base + cl;
 }
 
-enum { IO_SMEM = 0, IO_GLOBAL = 1 };
+enum { IO_SMEM = 0, IO_GLOBAL = 1, IO_DSMEM = 2 };
+
+// Thread-block cluster primitives (sm_90+ PTX): the barrier every thread of
+// every CTA of the cluster takes (release/acquire orders the shared-memory
+// writes before it with the remote reads after it), and an 8-byte load from
+// another CTA's shared memory at the same offset as `local` (a shared-window
+// address of this CTA) in CTA `rank`.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint64_t ld_dsmem_u64(uint32_t local, uint32_t rank) {
+    uint32_t ra;
+    uint64_t x;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(local), "r"(rank));
+    asm volatile("ld.shared::cluster.u64 %0, [%1];\n" : "=l"(x) : "r"(ra));
+    return x;
+}
+
+// Element l of this CTA's tile in the exchange round of a cluster-fused
+// transform of N = 2^K1 x 2^K2 (index = row << K2 | col; the column phase runs
+// stages 0 .. K1-1 on the row bits, the row phase stages K1 .. L-1 on the
+// column bits).  In the column phase CTA k holds columns
+// [k 2^xlogGc, (k+1) 2^xlogGc) of every row, at local index row << xlogGc |
+// col'; in the row phase rows [k 2^xlogGb, (k+1) 2^xlogGb) of every column,
+// at local index row' << K2 | col.  FROM_COLUMN: l indexes a row-phase tile
+// (the forward's exchange) whose data sits in the column-phase layout;
+// otherwise l indexes a column-phase tile (the inverse's exchange) whose data
+// sits in the row-phase layout.
+template <bool FROM_COLUMN>
+__device__ __forceinline__ uint64_t exchange_load(const TileCtx& c, uint32_t l) {
+    uint32_t owner, rl;
+    if (FROM_COLUMN) {
+        const uint32_t row = (uint32_t)c.b_base + (l >> c.xK2);
+        const uint32_t col = l & ((1u << c.xK2) - 1);
+        owner = col >> c.xlogGc;
+        rl = (row << c.xlogGc) | (col & ((1u << c.xlogGc) - 1));
+    } else {
+        const uint32_t row = l >> c.logGc;
+        owner = row >> c.xlogGb;
+        rl = ((row & ((1u << c.xlogGb) - 1)) << c.xK2) |
+             ((uint32_t)c.c_base + (l & ((1u << c.logGc) - 1)));
+    }
+    return ld_dsmem_u64(c.xsm + 8u * pad(rl), owner);
+}
 
 // One register round: stages s0+P .. s0+P+R-1 of the pass.  Each thread holds
 // 2^LOG_R elements = U = 2^(LOG_R-R) independent groups of 2^R; register index
@@ -186,7 +241,7 @@ enum { IO_SMEM = 0, IO_GLOBAL = 1 };
 // (stage_twiddles), `tw` pointing at it; WAIT_TW makes this round wait for
 // that copy after issuing its own loads.
 template <bool FWD, typename Wd, int AR, int LOG_R, int K, int P, int R, int SRC, int DST,
-          int NP = 1, bool ROW = false, bool TWS = false, bool WAIT_TW = false>
+          int NP = 1, bool ROW = false, bool TWS = false, bool WAIT_TW = false, bool PF = false>
 __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __restrict__ tw,
                                           const LimbDev& lc, const TileCtx& c) {
     constexpr int RN = 1 << LOG_R;
@@ -212,6 +267,21 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
     }
     const int sshift = ROW ? ELO : ELO + c.logGc;   // v stride in the tile
     const int gshift = ROW ? ELO : ELO + c.w;       // v stride in global memory
+    if constexpr (PF) {
+        // ask L1 for the round's twiddle lines before the data arrives:
+        // sub-stage k reads the 2^k pairs from entry hp << k (<= 128 bytes
+        // for k <= 3, one line when aligned)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const ulonglong2* p = tw + (hp[u] << k);
+#pragma unroll
+                for (int b = 0; b < ((16 << k) + 127) / 128; ++b)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + 8 * b));
+            }
+        }
+    }
     uint32_t pl[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) pl[u] = pad(lbase[u]);
@@ -231,6 +301,14 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
 #pragma unroll
                 for (int v = 0; v < (1 << R); ++v)
                     x[(v << (LOG_R - R)) | u] = (Wd)__ldg(p + ((uint64_t)v << gshift));
+            }
+        } else if (SRC == IO_DSMEM) {
+            // the forward's exchange is in its row phase (ROW), the inverse's
+            // in its column phase
+#pragma unroll
+            for (int reg = 0; reg < RN; ++reg) {
+                const int u = reg & (U - 1), v = reg >> (LOG_R - R);
+                x[reg] = (Wd)exchange_load<ROW>(c, lbase[u] | ((uint32_t)v << sshift));
             }
         } else {
             const uint64_t* smp = sm + pp * TEP;
@@ -298,6 +376,9 @@ __device__ __forceinline__ void ntt_round(uint64_t* sm, const ulonglong2* __rest
         }
     }
 
+    // every CTA of the cluster has read what it needs from this CTA's tile
+    // before this CTA overwrites it
+    if constexpr (SRC == IO_DSMEM) cluster_sync_all();
 #pragma unroll
     for (int pp = 0; pp < NP; ++pp) {
         if (NP > 1 && pp >= (int)c.np_valid) continue;

@@ -73,8 +73,9 @@ void timing_end(uint32_t slot, cudaStream_t s) {
         cudaEventRecord(g_tm[idx - 1].b, s);
 }
 
-static const char* kKernelNames[3] = {"ntt_pass_kernel", "ntt_pipe_kernel",
-                                      "ntt_tensor_inv_kernel"};
+static const char* kKernelNames[5] = {"ntt_pass_kernel", "ntt_pipe_kernel",
+                                      "ntt_tensor_inv_kernel", "ntt_cluster_kernel",
+                                      "ntt_cluster_tensor_kernel"};
 
 template <int KIND>
 __global__ void __launch_bounds__(256) int_mul_probe_kernel(uint32_t iters, uint32_t a,
@@ -259,8 +260,11 @@ extern "C" int hx_kernel_name(uint32_t kernel, char* buf, uint32_t len) {
         w = snprintf(buf, len, "%s<%u, %u, %u, %u>", kKernelNames[1], fwd, column, logR, K);
     else if (kind == 2)
         w = snprintf(buf, len, "%s<%u, %u, %u, %u>", kKernelNames[2], logR, K, tws, np);
+    else if ((kernel >> 12) & 1u)   // cluster-fused: K holds K1, bits 15-19 K2
+        w = snprintf(buf, len, "%s<%u, %u, %u>", kKernelNames[4], logR, K, (kernel >> 15) & 31u);
     else
-        return HX_ERR_ARG;
+        w = snprintf(buf, len, "%s<%u, %u, %u, %u>", kKernelNames[3], fwd, logR, K,
+                     (kernel >> 15) & 31u);
     return w < 0 || (uint32_t)w >= len ? HX_ERR_CAPACITY : HX_OK;
 }
 

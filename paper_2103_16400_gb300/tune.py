@@ -5,7 +5,8 @@ and names choosing "via a small number of trials" as future work (Section
 3.2).  Here the trials are the schedule: how the log2 N stages split into
 passes, the tile shape of each pass, elements per thread, and which kernel
 a pass runs (per-tile, persistent double-buffered, or per-tile with staged
-twiddles).  Every schedule computes the same result; `tune()` times
+twiddles) -- or whether both passes run as one cluster-fused launch, and
+with how many CTAs a cluster.  Every schedule computes the same result; `tune()` times
 candidates of the forward and of the inverse transform on the caller's plan
 and batch size with CUDA events and keeps the fastest of each: every
 single-pass schedule, and per split of the stages a coordinate search over
@@ -57,13 +58,34 @@ def pass_options(logN: int, K1: int, variants=VARIANTS) -> Tuple[List[Pass], Lis
     return firsts, seconds
 
 
+#: elements per thread of the cluster-fused kernels
+CLUSTER_LOGR = (4, 3)
+
+
+def cluster_options(logN: int) -> List[List[Pass]]:
+    """Cluster-fused schedules (pipe 3 on both passes): one launch of
+    clusters of 2^c CTAs per limb-transform, CTA k holding columns
+    [k 2^(K2-c), (k+1) 2^(K2-c)) in the column phase and rows
+    [k 2^(K1-c), (k+1) 2^(K1-c)) in the row phase, exchanging through
+    distributed shared memory."""
+    out = []
+    for K1 in range(6, 10):
+        K2 = logN - K1
+        if not 6 <= K2 <= 9:
+            continue
+        for c in (1, 2, 3, 4):
+            for r in CLUSTER_LOGR:
+                out.append([(0, K1, 0, K2 - c, r, 3, 1), (K1, K2, K1 - c, 0, r, 3, 1)])
+    return out
+
+
 def candidates(logN: int, variants=VARIANTS) -> List[List[Pass]]:
     """Every schedule worth trying for log2 N (validity is checked by the library)."""
     out = single_pass(logN, variants)
     for K1 in splits(logN):
         firsts, seconds = pass_options(logN, K1, variants)
         out += [[a, b] for a in firsts for b in seconds]
-    return out
+    return out + cluster_options(logN)
 
 
 def valid(plan: "capi.Plan", sched: List[Pass]) -> bool:
@@ -122,6 +144,7 @@ def covering(plan: "capi.Plan", variants=VARIANTS) -> List[List[Pass]]:
     second pass and each valid second pass with one valid first pass."""
     logN = plan.N.bit_length() - 1
     out = [s for s in single_pass(logN, variants) if valid(plan, s)]
+    out += [s for s in cluster_options(logN) if valid(plan, s)]
     for K1 in splits(logN):
         firsts, seconds = pass_options(logN, K1, variants)
         pair = _valid_pair(plan, firsts, seconds)
@@ -185,7 +208,7 @@ def _search(plan, timer, label: str, verbose: bool):
         timed.append((t, s))
         return t
 
-    for s in single_pass(logN):
+    for s in single_pass(logN) + cluster_options(logN):
         if valid(plan, s):
             run_keep(s)
     for K1 in splits(logN):

@@ -17,8 +17,10 @@ def test_kernel_names():
     assert capi.hx_kernel_name(kid(0, 0, 1, 4, 7, 1, 1)) == "ntt_pass_kernel<0, 1, 4, 7, 1, 1>"
     assert capi.hx_kernel_name(kid(1, 1, 0, 3, 9)) == "ntt_pipe_kernel<1, 0, 3, 9>"
     assert capi.hx_kernel_name(kid(2, 0, 0, 3, 9, 3)) == "ntt_tensor_inv_kernel<3, 9, 0, 3>"
-    with pytest.raises(capi.HexError):
-        capi.hx_kernel_name(3)
+    # cluster-fused transforms: kind 3, K1 in the K field, K2 in bits 15-19
+    assert capi.hx_kernel_name(kid(3, 1, 0, 4, 8, 0) | 8 << 15) == "ntt_cluster_kernel<1, 4, 8, 8>"
+    assert (capi.hx_kernel_name(kid(3, 0, 0, 4, 7, 1) | 9 << 15)
+            == "ntt_cluster_tensor_kernel<4, 7, 9>")
 
 
 def test_nothing_recorded_while_off():

@@ -1,6 +1,7 @@
 """The autotuner's host logic (no GPU): every candidate schedule runs the
 stages 0 .. log2 N - 1 exactly once, in order, as one pass (N <= 2^13) or a
-column pass then a row pass of 6 to 13 stages each; cache keys tell apart
+column pass then a row pass of 6 to 13 stages each, or a cluster-fused
+pair of 6 to 9 stages each with one cluster size; cache keys tell apart
 the GPU, N, the width mix and the batch; the cache survives a round trip."""
 import pytest
 
@@ -17,8 +18,15 @@ def test_candidates_cover_every_stage_once(logN):
         for p in sched:
             assert p[0] == s0                          # passes follow each other
             s0 += p[1]
-            assert (p[4], p[5], p[6]) in tune.VARIANTS
+            assert (p[4], p[5], p[6]) in tune.VARIANTS or p[5] == 3
         assert s0 == logN
+        if sched[0][5] == 3:                           # cluster-fused: both passes one launch
+            col, row = sched
+            assert row[5] == 3 and col[4] == row[4] and col[4] in tune.CLUSTER_LOGR
+            c = row[1] - col[3]
+            assert 1 <= c <= 4 and col[1] - row[2] == c    # same cluster size both ways
+            assert 6 <= col[1] <= 9 and 6 <= row[1] <= 9
+            continue
         if len(sched) == 1:
             assert logN <= 13 and sched[0][2] == sched[0][3] == 0
         else:
@@ -27,6 +35,7 @@ def test_candidates_cover_every_stage_once(logN):
             assert row[3] == 0 and 0 <= row[2] <= 5         # row tiles
             assert 6 <= col[1] <= 13 and 6 <= row[1] <= 13
     assert any(len(s) == 1 for s in cands) == (logN <= 13)
+    assert any(s[0][5] == 3 for s in cands) == (12 <= logN <= 18)
 
 
 def test_cache_keys_tell_workloads_apart():
