@@ -103,43 +103,101 @@ def slots_per_tensor_position(q):
     return SLOTS_TENSOR_NARROW if q < (1 << 30) else SLOTS_TENSOR_WIDE
 
 
-#: DRAM bytes (read + write) of one launch of the fused tensor / first
-#: inverse pass over one ciphertext pair at N = 65536 x 32 mixed limbs, from
-#: an ncu capture of the current kernel, keyed by (kernel, that pass of the
-#: inverse schedule).
-FUSED_TRAFFIC_BYTES = {
-    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[7, 9, 1, 0, 3, 0, 2]"): 151025152 + 22551296,
-}
+def kernel_source_hash():
+    """Short hash of the library's sources (kernels and host launch code): a
+    DRAM-traffic figure captured with ncu is reported only while the sources
+    it was captured from are the ones running."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_16400_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-def kernel_slots(kid, N, moduli, n_ct=1):
-    """Algorithmic IMAD slots of one launch of a timed kernel in the step:
-    a pass over its K stages (four polynomials forward, three inverse), or
-    the fused pass (the element-wise step plus its K inverse stages on three
-    polynomials per ciphertext pair).  An inverse pass that ends the
-    transform also scales by N^-1 (Algorithm GS's final loop): folded into
-    its last stage, that is one more Shoup product per butterfly there."""
+#: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) at N = 65536 x 32
+#: mixed limbs from ncu captures, keyed by (kernel name or "forward_call",
+#: schedule JSON, kernel_source_hash() of the captured build).  A key whose
+#: hash is not the running build's gives no figure (the field is null), so a
+#: changed kernel never reports stale traffic.  profiles/ records the
+#: capture commands.
+TRAFFIC_BYTES = {}
+
+
+def traffic_for(what, sched):
+    if sched is None:
+        return None
+    return TRAFFIC_BYTES.get((what, json.dumps([list(p) for p in sched]), kernel_source_hash()))
+
+
+#: The roofline's plain operation count: a Shoup butterfly on 64-bit words is
+#: 10 IMAD-class operations (the high word of W'X from four 32x32-bit partial
+#: products, the low words of W X and Q q from three each), on 32-bit words 3,
+#: each counted at the mad.lo issue rate; the memory side is one HBM read and
+#: one write of every coefficient (operands read, results written) at the
+#: measured copy bandwidth; the bound is the slower of the two.
+OPS_WIDE, OPS_NARROW = 10, 3
+
+
+def ops_per_butterfly(q):
+    return OPS_NARROW if q < (1 << 30) else OPS_WIDE
+
+
+def _kernel_shape(kid, N):
+    """(kind, forward, stages, ends the inverse, tensor-fused) of a kernel id."""
     kind, fwd, column, K = kid & 3, (kid >> 2) & 1, (kid >> 3) & 1, (kid >> 7) & 31
-    bfly = sum(N // 2 * K * slots_per_butterfly(q) for q in moduli)
-    if kind == 2:
-        return n_ct * (3 * bfly + sum(N * slots_per_tensor_position(q) for q in moduli))
-    if not fwd and (column or K == N.bit_length() - 1):
-        bfly += sum(N // 2 * slots_per_butterfly(q) for q in moduli)
+    if kind == 3:                                   # cluster-fused: K1 + K2 stages
+        K += (kid >> 15) & 31
+        return kind, fwd, K, not fwd, bool((kid >> 12) & 1)
+    return kind, fwd, K, (not fwd) and (column or K == N.bit_length() - 1), kind == 2
+
+
+def kernel_slots(kid, N, moduli, n_ct=1, per_butterfly=None):
+    """Algorithmic IMAD work of one launch of a timed kernel in the step: a
+    pass over its K stages (four polynomials forward, three inverse), a
+    cluster-fused launch over all stages, or a fused pass (the element-wise
+    tensor step plus its inverse stages on three polynomials per ciphertext
+    pair).  An inverse launch that ends the transform also scales by N^-1
+    (Algorithm GS's final loop): folded into its last stage, that is one
+    more Shoup product per butterfly there.  In IMAD slots by default; with
+    per_butterfly=ops_per_butterfly, the plain operation count (butterflies
+    and N^-1 products only)."""
+    kind, fwd, K, ends_inv, tensor = _kernel_shape(kid, N)
+    per = per_butterfly or slots_per_butterfly
+    bfly = sum(N // 2 * K * per(q) for q in moduli)
+    if ends_inv:
+        bfly += sum(N // 2 * per(q) for q in moduli)
+    if tensor:
+        extra = 0 if per_butterfly else sum(N * slots_per_tensor_position(q) for q in moduli)
+        return n_ct * (3 * bfly + extra)
     return (4 if fwd else 3) * n_ct * bfly
 
 
-#: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, both pass launches)
-#: of one forward call over 4 polynomials x 32 mixed limbs at N = 65536, from
-#: ncu captures (dram__bytes_* metrics, the current kernels with the column
-#: passes' limb launch order) of that call under each schedule listed; reported
-#: only when the tuned forward schedule is one of them (other kernels, other
-#: traffic).  Keyed by the schedule's JSON.
-FWD_TRAFFIC_BYTES = {
-    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]": 67257856 + 17679360 + 100657408 + 14364416,
-    "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 1]]": 67254784 + 17325312 + 100657152 + 14397440,
-    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]": 67323136 + 24393472 + 100595200 + 14092032,
-    "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]": 67322112 + 23800576 + 100591104 + 14021376,
-}
+def kernel_bytes(kid, N, n_limbs, n_ct=1):
+    """Algorithmic HBM bytes of one launch: a pass or a transform reads and
+    writes each coefficient once (four polynomials forward, three inverse);
+    the tensor-fused launch reads the seven operands (A0, A1, B0, B1, e0, e1,
+    e2) and writes its three outputs."""
+    kind, fwd, K, ends_inv, tensor = _kernel_shape(kid, N)
+    if tensor:
+        return 10 * 8 * N * n_limbs * n_ct
+    return 2 * (4 if fwd else 3) * 8 * N * n_limbs * n_ct
+
+
+def op_roofline(ops, nbytes, us, imad_rate, hbm_gbs):
+    """The roofline of `ops` integer operations and `nbytes` of HBM traffic
+    done in `us` microseconds: the slower side is the bound; achieved and
+    peak are that side's rate."""
+    t_int = ops / imad_rate * 1e6
+    t_hbm = nbytes / (hbm_gbs * 1e9) * 1e6
+    if t_int >= t_hbm:
+        return {"bound": "alu", "achieved": ops / (us * 1e-6) / 1e12, "peak": imad_rate / 1e12,
+                "unit": "T IMAD-op/s", "frac": t_int / us, "int_us": t_int, "hbm_us": t_hbm}
+    return {"bound": "hbm", "achieved": nbytes / (us * 1e-6) / 1e9, "peak": hbm_gbs,
+            "unit": "GB/s", "frac": t_hbm / us, "int_us": t_int, "hbm_us": t_hbm}
 
 
 def imad_slots_per_transform(N, moduli):
@@ -265,7 +323,7 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
-def ntt_rates_report(torch, step, dev_sets, imad_rate, iters=200):
+def ntt_rates_report(torch, step, dev_sets, imad_rate, hbm_gbs, iters=200):
     """The plain transforms of the step's plan timed on their own: the forward
     call (four polynomials, the step's inputs rotating over the input sets)
     and the inverse call (three polynomials from the addend sets, rotating --
@@ -297,21 +355,43 @@ def ntt_rates_report(torch, step, dev_sets, imad_rate, iters=200):
     inv_us = timed(lambda i: capi.hx_ntt_inverse(step.plan, R, dev_sets[i % len(dev_sets)][1],
                                                  3, 1, 1, st))
     warm_ms = timed(lambda i: step.run(0)) / 1e3
-    slots_f = sum(imad_slots_per_transform(N, moduli))
-    slots_i = slots_f + sum(N // 2 * slots_per_butterfly(q) for q in moduli)   # + N^-1
-    t_f, t_i = fwd_us / (4 * nl), inv_us / (3 * nl)       # us per limb-transform
+    out = fwd_inv_figures(N, moduli, fwd_us, inv_us, imad_rate, hbm_gbs)
+    out.update({"schedules": {"forward": step.plan.schedule(step.plan.FORWARD),
+                              "inverse": step.plan.schedule(step.plan.INVERSE)},
+                "l2_warm_step": {"ms_per_step": warm_ms,
+                                 "limb_transforms_per_s": 7 * nl / (warm_ms * 1e-3),
+                                 "how": "the timed step on one input set, no rotation"},
+                "how": f"{iters} calls each, CUDA events, inputs rotating over "
+                       f"{len(dev_sets)} sets (> L2); *_frac: operation-count roofline, "
+                       f"*_frac_slots: IMAD-slot model"})
+    return out
+
+
+def fwd_inv_figures(N, moduli, fwd_us, inv_us, imad_rate, hbm_gbs):
+    """Rates and roofline fractions of a forward call over four polynomials
+    (fwd_us) and an inverse call over three (inv_us, with the N^-1 scaling)
+    on all limbs: the operation-count roofline of each call (the slower of
+    its integer and HBM sides) and of the two together, and the IMAD-slot
+    model's fraction of the two together."""
+    nl = len(moduli)
+    slots_f = sum(imad_slots_per_transform(N, moduli))        # one polynomial, all limbs
+    slots_i = slots_f + sum(N // 2 * slots_per_butterfly(q) for q in moduli)
+    t_f, t_i = fwd_us / (4 * nl), inv_us / (3 * nl)           # us per limb-transform
+    logn = N.bit_length() - 1
+    ops_f = sum(N // 2 * logn * ops_per_butterfly(q) for q in moduli)
+    ops_i = ops_f + sum(N // 2 * ops_per_butterfly(q) for q in moduli)
+    rf = op_roofline(4 * ops_f, 4 * 16 * N * nl, fwd_us, imad_rate, hbm_gbs)
+    ri = op_roofline(3 * ops_i, 3 * 16 * N * nl, inv_us, imad_rate, hbm_gbs)
+    bound_us = max(rf["int_us"], rf["hbm_us"]) + max(ri["int_us"], ri["hbm_us"])
     return {"forward_us": fwd_us, "inverse_us": inv_us,
             "forward_limb_transforms_per_s": 1e6 / t_f,
             "inverse_limb_transforms_per_s": 1e6 / t_i,
             "fwd_plus_inv_pairs_per_s": 1e6 / (t_f + t_i),
-            "roofline_fwd_plus_inv_frac": (slots_f + slots_i) / ((t_f + t_i) * 1e-6) / imad_rate,
-            "schedules": {"forward": step.plan.schedule(step.plan.FORWARD),
-                          "inverse": step.plan.schedule(step.plan.INVERSE)},
-            "l2_warm_step": {"ms_per_step": warm_ms,
-                             "limb_transforms_per_s": 7 * nl / (warm_ms * 1e-3),
-                             "how": "the timed step on one input set, no rotation"},
-            "how": f"{iters} calls each, CUDA events, inputs rotating over "
-                   f"{len(dev_sets)} sets (> L2)"}
+            "fwd_plus_inv_frac": bound_us / (fwd_us + inv_us),
+            "fwd_plus_inv_frac_slots":
+                (4 * slots_f + 3 * slots_i) / ((fwd_us + inv_us) * 1e-6) / imad_rate,
+            "forward_frac": rf["frac"], "forward_bound": rf["bound"],
+            "inverse_frac": ri["frac"], "inverse_bound": ri["bound"]}
 
 
 def eltwise_report(torch, N=1 << 16, nl=32, P=4, reps=20):
@@ -496,7 +576,7 @@ class ClockSampler:
     """Samples SM clock and clock-event reasons during the timed region, by
     NVML through ctypes (read-only queries), else by nvidia-smi."""
 
-    def __init__(self, device_index=0, period=0.02):
+    def __init__(self, device_index=0, period=0.004):
         self.period, self.samples, self.reasons = period, [], set()
         self.max_mhz = None
         self._stop = threading.Event()
@@ -850,10 +930,24 @@ def main():
     with ClockSampler(local) as clocks:
         t0.record(stream)
         for i in range(args.steps):
-            step.run(i, record=True)
+            step.run(i)
         t1.record(stream)
         torch.cuda.synchronize()
     launches = capi.hx_launch_count() - launches0
+    total_ms = t0.elapsed_time(t1)
+    total_ms = shard.max_over_ranks(total_ms, device="cuda")
+    barrier()
+
+    # the two calls of the step timed apart (CUDA events between them), in
+    # a region of their own after the contract's timed region
+    calls_steps = min(args.steps, 200)
+    step.fwd_events.clear()
+    step.inv_events.clear()
+    for i in range(calls_steps):
+        step.run(i, record=True)
+    torch.cuda.synchronize()
+    fwd_ms = [a.elapsed_time(b) for a, b in step.fwd_events]
+    inv_ms = [a.elapsed_time(b) for a, b in step.inv_events]
 
     # kernel-timing region: the same steps again with the library's events
     # around every launch (each pair adds a start-up bubble of a microsecond
@@ -866,37 +960,44 @@ def main():
     torch.cuda.synchronize()
     capi.hx_timing_enable(False)
     timed = capi.hx_timing_read(4 * kt_steps + 64)
-    total_ms = t0.elapsed_time(t1)
-    fwd_ms = [a.elapsed_time(b) for a, b in step.fwd_events]
-    inv_ms = [a.elapsed_time(b) for a, b in step.inv_events]
-    total_ms = shard.max_over_ranks(total_ms, device="cuda")
     barrier()
 
     per_step_units = 7 * nl
     value = per_step_units * args.steps * ws / (total_ms / 1e3)
 
-    # roofline of the forward NTT call (4 polynomials, two pass launches; kept
-    # as roofline_forward_call), IMAD-bound; peak = mad.lo issue rate probed live
+    # Rooflines.  Primary figure: the operation count (10 IMAD operations per
+    # 64-bit-word butterfly, 3 per 32-bit-word one, at the live mad.lo rate)
+    # against one HBM read + write per coefficient (measured copy
+    # bandwidth), the slower side being the bound.  Second figure
+    # (`slots`): the IMAD-slot model, which weighs each multiply form by its
+    # measured issue cost (mad.hi and mad.wide issue at half the mad.lo rate
+    # or less).
     imad_rate, _ = capi.hx_probe_int_mul_rate("mad.lo", 8192)
+    hbm_gbs, hbm_src = hbm_peak_gbs()
+    peak_source = (f"IMAD: hx_probe_int_mul_rate mad.lo.u32, measured live; HBM: "
+                   f"{hbm_gbs:.0f} GB/s copy bandwidth ({hbm_src}, MEASURED_PEAKS.json)")
+    logn = N.bit_length() - 1
     fwd_call_ms = float(np.mean(fwd_ms))
-    alg_slots = 4 * sum(imad_slots_per_transform(N, wl.moduli))
-    achieved = alg_slots / (fwd_call_ms * 1e-3)
+    inv_call_ms = float(np.mean(inv_ms))
+    fwd_ops = 4 * sum(N // 2 * logn * ops_per_butterfly(q) for q in wl.moduli)
     fwd_bytes = 4 * 16 * N * nl
-    fwd_sched = getattr(step, "tuned", {}).get("forward", {}).get("forward")
-    traffic = (FWD_TRAFFIC_BYTES.get(json.dumps(fwd_sched)) if (N, nl) == (1 << 16, 32)
-               else None)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": imad_rate / 1e12,
-                "unit": "T IMAD-slot/s", "frac": achieved / imad_rate, "traffic": traffic,
-                "traffic_unit": "bytes per forward call (2 launches), ncu",
-                "alg_bytes_per_call": fwd_bytes,
-                "kernel": "hx_ntt_forward, 4 polys x 32 limbs (ntt pass kernels, 2 launches)",
-                "fwd_call_us": fwd_call_ms * 1e3,
-                "alg_slots_per_call": alg_slots,
-                "hbm_gbs_algorithmic": fwd_bytes / (fwd_call_ms * 1e-3) / 1e9,
-                "dram_gbs_measured": (traffic / (fwd_call_ms * 1e-3) / 1e9) if traffic else None,
-                "peak_source": "hx_probe_int_mul_rate mad.lo.u32 (1 slot), measured live",
-                "schedules": {k: v.get("forward" if k == "forward" else "inverse")
-                              for k, v in getattr(step, "tuned", {}).items()}}
+    alg_slots = 4 * sum(imad_slots_per_transform(N, wl.moduli))
+    fwd_sched = step.plan.schedule(step.plan.FORWARD)
+    inv_sched = step.plan.schedule(step.plan.INVERSE)
+    traffic = traffic_for("forward_call", fwd_sched) if (N, nl) == (1 << 16, 32) else None
+    roofline_forward_call = dict(
+        op_roofline(fwd_ops, fwd_bytes, fwd_call_ms * 1e3, imad_rate, hbm_gbs),
+        traffic=traffic,
+        traffic_unit="DRAM bytes per forward call (ncu, this build's sources), else null",
+        kernel="hx_ntt_forward, 4 polys x 32 limbs",
+        fwd_call_us=fwd_call_ms * 1e3, alg_ops_per_call=fwd_ops, alg_bytes_per_call=fwd_bytes,
+        slots={"frac": alg_slots / (fwd_call_ms * 1e-3) / imad_rate,
+               "achieved": alg_slots / (fwd_call_ms * 1e-3) / 1e12, "peak": imad_rate / 1e12,
+               "unit": "T IMAD-slot/s", "alg_slots_per_call": alg_slots},
+        dram_gbs_measured=(traffic / (fwd_call_ms * 1e-3) / 1e9) if traffic else None,
+        peak_source=peak_source,
+        schedules={"forward": [list(p) for p in fwd_sched],
+                   "inverse": [list(p) for p in inv_sched]})
 
     # every kernel of the step timed live (library events around each launch
     # in the kernel-timing region); the roofline object is the dominant kernel's
@@ -910,35 +1011,56 @@ def main():
     for kid, k in kernels.items():
         k["avg_us"] = k["total_ms"] / k["launches"] * 1e3
         k["share"] = k["total_ms"] / timed_total
+        k["alg_ops_per_launch"] = kernel_slots(kid, N, wl.moduli, per_butterfly=ops_per_butterfly)
+        k["alg_bytes_per_launch"] = kernel_bytes(kid, N, nl)
+        r = op_roofline(k["alg_ops_per_launch"], k["alg_bytes_per_launch"], k["avg_us"],
+                        imad_rate, hbm_gbs)
+        k["bound"], k["frac"] = r["bound"], r["frac"]
         k["alg_slots_per_launch"] = kernel_slots(kid, N, wl.moduli)
-        k["achieved_T_slots_per_s"] = k["alg_slots_per_launch"] / (k["avg_us"] * 1e-6) / 1e12
-        k["frac"] = k["achieved_T_slots_per_s"] * 1e12 / imad_rate
-    roofline_forward_call = roofline
+        k["frac_slots"] = k["alg_slots_per_launch"] / (k["avg_us"] * 1e-6) / imad_rate
+    roofline = roofline_forward_call
     if kernels:
         dom_id = max(kernels, key=lambda i: kernels[i]["total_ms"])
         dom = kernels[dom_id]
-        inv_sched = getattr(step, "tuned", {}).get("inverse", {}).get("inverse")
-        dom_traffic = None
-        if (dom_id & 3) == 2 and inv_sched and (N, nl) == (1 << 16, 32):
-            dom_traffic = FUSED_TRAFFIC_BYTES.get((dom["kernel"], json.dumps(inv_sched[-1])))
-        dom_bytes = (10 if (dom_id & 3) == 2 else 2 * (4 if (dom_id >> 2) & 1 else 3)) * 8 * N * nl
-        roofline = {"bound": "alu", "achieved": dom["achieved_T_slots_per_s"],
-                    "peak": imad_rate / 1e12, "unit": "T IMAD-slot/s", "frac": dom["frac"],
-                    "traffic": dom_traffic,
-                    "traffic_unit": "DRAM bytes per launch (ncu, same kernel and workload)",
-                    "kernel": dom["kernel"], "launches": dom["launches"],
-                    "avg_launch_us": dom["avg_us"], "share_of_timed_kernels": dom["share"],
-                    "alg_slots_per_launch": dom["alg_slots_per_launch"],
-                    "alg_bytes_per_launch": dom_bytes,
-                    "hbm_gbs_algorithmic": dom_bytes / (dom["avg_us"] * 1e-6) / 1e9,
-                    "dram_gbs_measured": (dom_traffic / (dom["avg_us"] * 1e-6) / 1e9
-                                          if dom_traffic else None),
-                    "peak_source": roofline_forward_call["peak_source"],
-                    "timing": f"CUDA events recorded by the library around every launch, on "
-                              f"the launching stream, over {kt_steps} steps right after the "
-                              f"timed region (same inputs, stream and schedules); each "
-                              f"duration includes its launch's start-up",
-                    "schedules": roofline_forward_call["schedules"]}
+        r = op_roofline(dom["alg_ops_per_launch"], dom["alg_bytes_per_launch"], dom["avg_us"],
+                        imad_rate, hbm_gbs)
+        dom_traffic = traffic_for(dom["kernel"], inv_sched if not (dom_id >> 2) & 1
+                                  else fwd_sched) if (N, nl) == (1 << 16, 32) else None
+        roofline = dict(
+            r, traffic=dom_traffic,
+            traffic_unit="DRAM bytes per launch (ncu, this build's sources), else null",
+            kernel=dom["kernel"], launches=dom["launches"], avg_launch_us=dom["avg_us"],
+            share_of_timed_kernels=dom["share"], alg_ops_per_launch=dom["alg_ops_per_launch"],
+            alg_bytes_per_launch=dom["alg_bytes_per_launch"],
+            slots={"frac": dom["frac_slots"],
+                   "achieved": dom["alg_slots_per_launch"] / (dom["avg_us"] * 1e-6) / 1e12,
+                   "peak": imad_rate / 1e12, "unit": "T IMAD-slot/s",
+                   "alg_slots_per_launch": dom["alg_slots_per_launch"]},
+            dram_gbs_measured=(dom_traffic / (dom["avg_us"] * 1e-6) / 1e9
+                               if dom_traffic else None),
+            peak_source=peak_source,
+            timing=f"CUDA events recorded by the library around every launch, on the "
+                   f"launching stream, over {kt_steps} steps after the timed region (same "
+                   f"inputs, stream and schedules); each duration includes its launch's "
+                   f"start-up",
+            forward_call={"frac": roofline_forward_call["frac"],
+                          "bound": roofline_forward_call["bound"],
+                          "frac_slots": roofline_forward_call["slots"]["frac"],
+                          "us": fwd_call_ms * 1e3},
+            schedules=roofline_forward_call["schedules"])
+
+    # the plain forward and inverse calls on their own: the goal's forward +
+    # inverse figure, carried inside the roofline object as well
+    rates = None
+    if rank == 0:
+        try:
+            rates = ntt_rates_report(torch, step, dev_sets, imad_rate, hbm_gbs)
+            roofline["fwd_inv"] = {k: rates[k] for k in (
+                "forward_us", "inverse_us", "fwd_plus_inv_pairs_per_s", "fwd_plus_inv_frac",
+                "fwd_plus_inv_frac_slots", "forward_frac", "inverse_frac")}
+        except Exception as e:               # noqa: BLE001 -- reported, not hidden
+            rates = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.synchronize()
 
     # end to end through the public API with host buffers: every step uploads
     # its inputs from pinned host memory and downloads its three results; the
@@ -991,7 +1113,8 @@ def main():
                       "tensor_inverse_us": float(np.mean(inv_ms)) * 1e3,
                       "tensor_inverse_limb_transforms_per_s":
                           3 * nl / (float(np.mean(inv_ms)) * 1e-3),
-                      "how": "CUDA events around each call inside the timed region"},
+                      "how": f"CUDA events around each call, {calls_steps} steps in a "
+                             f"region after the timed one"},
             "gpu_launches": launches,
             "clocks": clocks.summary()}
     # the secondary reports run on rank 0 only; the other ranks wait.  A
@@ -1003,7 +1126,7 @@ def main():
             line[key] = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
-        report("ntt_rates", lambda t: ntt_rates_report(t, step, dev_sets, imad_rate))
+        line["ntt_rates"] = rates
         report("eltwise", eltwise_report)
     if rank == 0 and not args.no_ragged:
         report("batched", ragged_report)

@@ -229,6 +229,10 @@ int hx_eltwise_fma_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* 
  * hx_poly_mul: negacyclic product r = a * b in R_q per limb, composed as in
  *   the paper's Listing 4: forward NTT of a and of b in place with output in
  *   [0, 4q), EltwiseMultMod with input_mod_factor 4, inverse NTT to [0, q).
+ *   When the plan's inverse schedule starts with a per-tile row pass (or a
+ *   single pass), the element-wise product runs inside that pass (the
+ *   kernel-sequence fusion the paper's Conclusion points to): the product
+ *   never goes to HBM and one launch disappears; the result is the same.
  *   d_a and d_b are overwritten with their transforms; d_result may equal
  *   d_a.  All [n_polys][plan n_limbs][N].
  *
@@ -380,13 +384,15 @@ int hx_ntt_ragged(const hx_ragged_item* h_items, uint32_t n_items, uint32_t dire
  *   with input_mod_factor 4, inverse NTT to [0, q)).  Items may differ in N
  *   and moduli (every modulus below 2^61).  Operands are read, never
  *   written: the forward transforms go out of place into the workspace and
- *   the inverse writes the result.  The whole set runs as five kernels on
- *   `stream` (two forward passes, one product, two inverse passes).
+ *   the inverse writes the result.  The whole set runs as four kernels on
+ *   `stream`: two forward passes, then the inverse's two passes, the first
+ *   of which computes the element-wise product while it stages each tile
+ *   (the product never goes to HBM).
  *   hx_polymul_item: plan; d_a, d_b, d_result: device [n_polys][limbs][N]
  *   (d_result may equal d_a or d_b); n_polys >= 1.
  *   d_workspace: caller-owned device memory, 256-byte aligned, at least the
  *   size hx_polymul_ragged_workspace reports (twice the operand size plus
- *   32 bytes per tile); it holds the spectra, the tile lists and the work
+ *   32 to 48 bytes per tile and pass); it holds the spectra, the tile lists and the work
  *   counters, so the library allocates no device memory.  A workspace may be
  *   reused by calls ordered on one stream, not by concurrent ones.  The tile
  *   lists are written on the host into page-locked staging buffers that the

@@ -112,6 +112,70 @@ __global__ void __maxnreg__(64) ragged_pass_kernel(const RagTile* __restrict__ t
 
 static const size_t kRagSmem = padded(2048) * sizeof(uint64_t);
 
+// The inverse's first pass of a ragged product: the tile of a b mod q (both
+// spectra from the forward passes, below 4q) computed in the staging step,
+// then the row (or single) pass's stages -- the element-wise product never
+// goes to HBM.
+struct MulRagTile {
+    const uint64_t* a;    // this transform's first spectrum, element 0
+    const uint64_t* b;    // its second spectrum
+    uint64_t* out;        // its result
+    const LimbDev* lc;
+    uint32_t tile;
+    uint8_t kind;         // RK_S10, RK_S11 or a row kind
+    uint8_t L;
+    uint8_t last;
+    uint8_t out_mf;
+    uint64_t pad_;
+};
+static_assert(sizeof(MulRagTile) == 48, "descriptor is 48 bytes");
+
+template <int LOG_R, int K>
+__device__ __forceinline__ void rag_mul_tile(uint64_t* sm, const MulRagTile& d) {
+    const int L = d.L;
+    const int s0 = K >= L ? 0 : L - K;
+    const int logGb = K >= L ? 0 : 11 - K;
+    const int logTE = logGb + K;
+    TileCtx c;
+    c.gin = d.a;
+    c.gin2 = d.b;
+    c.mul_mf = 4;
+    c.gout = d.out;
+    c.b_base = (uint64_t)d.tile << logGb;
+    c.c_base = 0;
+    c.L = L;
+    c.s0 = s0;
+    c.logGc = 0;
+    c.logGb = logGb;
+    c.w = 0;
+    c.nthreads = (1u << logTE) >> LOG_R;
+    c.out_mf = d.out_mf;
+    c.last = d.last != 0;
+    const LimbDev lc = *d.lc;
+    process_tile<false, false, LOG_R, K, 1, false, true>(sm, c, lc, 1u << logTE);
+}
+
+__global__ void __maxnreg__(64) ragged_mul_inv_kernel(const MulRagTile* __restrict__ tiles,
+                                                      uint32_t n, uint32_t* counter) {
+    extern __shared__ uint64_t sm[];
+    __shared__ uint32_t s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t t = s_next;
+        if (t >= n) return;
+        const MulRagTile d = tiles[t];
+        switch (d.kind) {
+            case RK_S10: rag_mul_tile<2, 10>(sm, d); break;
+            case RK_S11: rag_mul_tile<3, 11>(sm, d); break;
+            case RK_R7: rag_mul_tile<3, 7>(sm, d); break;
+            case RK_R8: rag_mul_tile<3, 8>(sm, d); break;
+            default: rag_mul_tile<3, 9>(sm, d); break;
+        }
+        __syncthreads();   // tile finished with shared memory and s_next
+    }
+}
+
 }  // namespace hx
 
 using namespace hx;
@@ -136,6 +200,14 @@ static int rag_grid(bool fwd) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ragged_pass_kernel<true>, 256, kRagSmem);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ragged_pass_kernel<false>, 256, kRagSmem);
+    return std::max(1, per) * std::max(1, sms);
+}
+
+static int rag_mul_grid() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ragged_mul_inv_kernel, 256, kRagSmem);
     return std::max(1, per) * std::max(1, sms);
 }
 
@@ -439,40 +511,17 @@ extern "C" int hx_batch_run_static(const hx_ragged_item* items, uint32_t n_items
 // primitive).  For every item, c = a * b in R_q per the paper's Listing 4:
 // forward NTTs of a and b written out of place into the workspace (outputs
 // in [0, 4q)), the element-wise product with input_mod_factor 4, and the
-// inverse NTT written straight into the result.  Items may differ in N and
-// moduli; the whole set is five kernel launches (two forward passes, one
-// product, two inverse passes).  The workspace holds the spectra, the tile
+// inverse NTT written straight into the result.  The product runs inside the
+// inverse's first pass (its staging step reads both spectra).  Items may
+// differ in N and moduli; the whole set is four kernel launches (two forward
+// passes, two inverse passes).  The workspace holds the spectra, the tile
 // lists and the work counters, so the library allocates nothing.
 // ---------------------------------------------------------------------------
 namespace hx {
 
-struct MulTile {   // a[i] <- a[i] * b[i] mod q for i < count (count even)
-    uint64_t* a;
-    const uint64_t* b;
-    const LimbDev* lc;
-    uint32_t count;
-    uint32_t pad;
-};
-static_assert(sizeof(MulTile) == 32, "descriptor is 32 bytes");
-
-__global__ void __launch_bounds__(256) mul_tiles_kernel(const MulTile* __restrict__ tiles) {
-    const MulTile d = tiles[blockIdx.x];
-    const uint64_t q = d.lc->q;
-    const Barrett br{q, d.lc->barrett_k, d.lc->barrett_qm1};
-    ulonglong2* A = reinterpret_cast<ulonglong2*>(d.a);
-    const ulonglong2* B = reinterpret_cast<const ulonglong2*>(d.b);
-    for (uint32_t i = threadIdx.x; i < d.count / 2; i += blockDim.x) {
-        ulonglong2 x = A[i];
-        const ulonglong2 y = B[i];
-        x.x = barrett_mulmod(small_mod<4>(x.x, q), small_mod<4>(y.x, q), br);
-        x.y = barrett_mulmod(small_mod<4>(x.y, q), small_mod<4>(y.y, q), br);
-        A[i] = x;
-    }
-}
-
 struct PolymulLayout {
     uint64_t spectra = 0;      // bytes of A and B slots
-    uint64_t fA = 0, fB = 0, iA = 0, iB = 0, mul = 0;   // descriptor counts
+    uint64_t fA = 0, fB = 0, iA = 0, iB = 0;   // descriptor counts (iA: MulRagTile)
     uint64_t tiles_off = 0, total = 0;
 };
 
@@ -498,12 +547,11 @@ static int polymul_layout(const hx_polymul_item* items, uint32_t n, PolymulLayou
             L->fB += 2 * transforms * tiles;
             L->iB += transforms * tiles;
         }
-        L->mul += transforms * std::max<uint64_t>(1, p->N / 2048);
     }
     L->tiles_off = 256 + L->spectra;
-    L->total = L->tiles_off + (L->fA + L->fB + L->iA + L->iB) * sizeof(RagTile) +
-               L->mul * sizeof(MulTile);
-    if (L->fA + L->fB >= (1ull << 32) || L->mul >= (1ull << 31)) return HX_ERR_ARG;
+    L->total = L->tiles_off + (L->fA + L->fB + L->iB) * sizeof(RagTile) +
+               L->iA * sizeof(MulRagTile);
+    if (L->fA + L->fB >= (1ull << 32) || L->iA + L->iB >= (1ull << 32)) return HX_ERR_ARG;
     return HX_OK;
 }
 
@@ -586,19 +634,19 @@ extern "C" int hx_polymul_ragged(const hx_polymul_item* items, uint32_t n_items,
     if (workspace_bytes < L.total) return HX_ERR_CAPACITY;
     unsigned char* ws = (unsigned char*)d_workspace;
     uint32_t* counters = (uint32_t*)ws;
-    // descriptors, in launch order: fwd A, fwd B, inv A, inv B, then products
+    // descriptors, in launch order: fwd A, fwd B, inv B, then the product-
+    // fused first inverse pass (48-byte descriptors, kept last for alignment)
     const size_t host_bytes =
-        (L.fA + L.fB + L.iA + L.iB) * sizeof(RagTile) + L.mul * sizeof(MulTile);
+        (L.fA + L.fB + L.iB) * sizeof(RagTile) + L.iA * sizeof(MulRagTile);
     int dev = 0;
     cudaGetDevice(&dev);
     DescStaging* stage = staging_acquire(host_bytes, dev);
     if (!stage) return HX_ERR_NOMEM;
     RagTile* fA = (RagTile*)stage->buf;
     RagTile* fB = fA + L.fA;
-    RagTile* iA = fB + L.fB;
-    RagTile* iB = iA + L.iA;
-    MulTile* mt = (MulTile*)(iB + L.iB);
-    uint64_t nfA = 0, nfB = 0, niA = 0, niB = 0, nm = 0;
+    RagTile* iB = fB + L.fB;
+    MulRagTile* iA = (MulRagTile*)(iB + L.iB);
+    uint64_t nfA = 0, nfB = 0, niA = 0, niB = 0;
     uint64_t* spec = (uint64_t*)(ws + 256);
     for (uint32_t i = 0; i < n_items; ++i) {
         const hx_polymul_item& it = items[i];
@@ -623,16 +671,14 @@ extern "C" int hx_polymul_ragged(const hx_polymul_item* items, uint32_t n_items,
                         fB[nfB++] = RagTile{A + off, A + off, lc, t, (uint8_t)k2, lg, 1, 4};
                         fB[nfB++] = RagTile{B + off, B + off, lc, t, (uint8_t)k2, lg, 1, 4};
                     }
-                    // inverse: A -> result (row/single pass first), out range [0, q)
-                    iA[niA++] = RagTile{A + off, it.d_result + off, lc, t,
-                                        (uint8_t)(single ? k1 : k2), lg, single, 1};
+                    // inverse of A B (the product in the first pass's staging):
+                    // -> result (row/single pass first), out range [0, q)
+                    iA[niA++] = MulRagTile{A + off, B + off, it.d_result + off, lc, t,
+                                           (uint8_t)(single ? k1 : k2), lg, single, 1, 0};
                     if (!single)
                         iB[niB++] = RagTile{it.d_result + off, it.d_result + off, lc, t,
                                             (uint8_t)k1, lg, 1, 1};
                 }
-                const uint32_t chunk = (uint32_t)std::min<uint64_t>(p->N, 2048);
-                for (uint64_t c = 0; c < p->N; c += chunk)
-                    mt[nm++] = MulTile{A + off + c, B + off + c, lc, chunk, 0};
             }
         }
     }
@@ -658,14 +704,14 @@ extern "C" int hx_polymul_ragged(const hx_polymul_item* items, uint32_t n_items,
     };
     cudaError_t e = pass(true, dt, L.fA, counters, gf);
     if (e == cudaSuccess) e = pass(true, dt + L.fA, L.fB, counters + 1, gf);
-    if (e == cudaSuccess) {
-        const MulTile* dm = (const MulTile*)(dt + L.fA + L.fB + L.iA + L.iB);
-        mul_tiles_kernel<<<(unsigned)L.mul, 256, 0, s>>>(dm);
+    if (e == cudaSuccess && L.iA) {
+        const MulRagTile* dm = (const MulRagTile*)(dt + L.fA + L.fB + L.iB);
+        const unsigned g = (unsigned)std::min<uint64_t>(L.iA, (uint64_t)rag_mul_grid());
+        ragged_mul_inv_kernel<<<g, 256, kRagSmem, s>>>(dm, (uint32_t)L.iA, counters + 2);
         count_launch();
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = pass(false, dt + L.fA + L.fB, L.iA, counters + 2, gi);
-    if (e == cudaSuccess) e = pass(false, dt + L.fA + L.fB + L.iA, L.iB, counters + 3, gi);
+    if (e == cudaSuccess) e = pass(false, dt + L.fA + L.fB, L.iB, counters + 3, gi);
     return e == cudaSuccess ? HX_OK : HX_ERR_CUDA;
 }
 

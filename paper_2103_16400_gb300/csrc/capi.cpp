@@ -255,6 +255,11 @@ int hx_poly_mul(hx_plan_t plan, uint64_t* r, uint64_t* a, uint64_t* b, uint32_t 
     int st = hx_ntt_forward(plan, a, a, n_polys, 1, 4, stream);
     if (st != HX_OK) return st;
     if ((st = hx_ntt_forward(plan, b, b, n_polys, 1, 4, stream)) != HX_OK) return st;
+    // the product computed in the inverse's first pass when its schedule
+    // allows (a per-tile row pass), else a separate element-wise pass
+    if (mul_fusable(plan->cfg_inv))
+        return cuda_status(launch_mul_inverse(plan, r, a, b, n_polys, 4, plan->cfg_inv,
+                                              (cudaStream_t)stream));
     st = cuda_status(launch_eltwise(ELT_MULT, r, a, b, nullptr, plan->N, plan->moduli.data(),
                                     plan->n_limbs, n_polys, 4, (cudaStream_t)stream));
     if (st != HX_OK) return st;

@@ -86,7 +86,8 @@ void count_launch(uint64_t n = 1);
 // pass, 3 cluster-fused transform), 2 forward, 3 column, 4-6 logR, 7-11 K
 // (K1 for kind 3), 12-13 polynomials (outputs for the fused pass; for kind 3
 // bit 12 marks the tensor-fused inverse) per block, 14 staged twiddles,
-// 15-19 K2 (kind 3).
+// 15-19 K2 (kind 3); for kind 0, bit 15 marks the inverse's first pass with
+// the dyadic product fused in.
 uint32_t timing_begin(cudaStream_t s, uint32_t kernel);
 void timing_end(uint32_t slot, cudaStream_t s);
 
@@ -111,6 +112,14 @@ bool cfg_supported(int logN, const NttCfg& cfg);
 // (forward outputs, < in_mf q) and E = [3][n_ct].. (< q).  cudaErrorNotSupported
 // when the schedule's first inverse pass is not a per-tile row pass.
 bool tensor_fusable(const NttCfg& cfg);
+// Inverse transform of the dyadic product a_i b_i mod q (a, b forward
+// outputs below in_mf q) with the product computed in the inverse's first
+// pass: out = InvNTT(a . b).  cudaErrorNotSupported when that pass is not a
+// per-tile row pass (mul_fusable).
+bool mul_fusable(const NttCfg& cfg);
+cudaError_t launch_mul_inverse(const hx_plan_s* plan, uint64_t* out, const uint64_t* a,
+                               const uint64_t* b, uint32_t n_polys, uint32_t in_mf,
+                               const NttCfg& cfg, cudaStream_t stream);
 cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const uint64_t* A,
                                   const uint64_t* E, uint32_t n_ct, const uint64_t* h_scalars,
                                   uint32_t in_mf, const NttCfg& cfg, cudaStream_t stream);

@@ -241,16 +241,19 @@ static int resident_blocks(PassKernel k, int threads, size_t smem, int* sms) {
 }
 
 // Kernel id of a pass for launch timing (layout in hx_internal.h).
-static uint32_t pass_kernel_id(bool fwd, const PassCfg& p) {
+static uint32_t pass_kernel_id(bool fwd, const PassCfg& p, bool mul = false) {
     return (p.pipe == 1 ? 1u : 0u) | (fwd ? 4u : 0u) | (p.logGc > 0 ? 8u : 0u) |
            ((uint32_t)p.logR << 4) | ((uint32_t)p.K << 7) | ((uint32_t)p.np << 12) |
-           (p.pipe == 2 ? 1u << 14 : 0u);
+           (p.pipe == 2 ? 1u << 14 : 0u) | (mul ? 1u << 15 : 0u);
 }
 
-// Launches one pass of a schedule over n_polys polynomials.
+// Launches one pass of a schedule over n_polys polynomials.  With mul_b the
+// pass is the inverse's first (row) pass with the dyadic product of `in`
+// and mul_b (both below mul_mf q) computed in its staging step.
 static cudaError_t launch_pass(const hx_plan_s* plan, const PassCfg& p, uint64_t* out,
                                const uint64_t* in, uint32_t n_polys, bool forward, bool last,
-                               uint32_t out_mf, cudaStream_t stream) {
+                               uint32_t out_mf, cudaStream_t stream,
+                               const uint64_t* mul_b = nullptr, uint32_t mul_mf = 1) {
     const int L = plan->logN;
     PassArgs a;
     a.out = out;
@@ -274,13 +277,24 @@ static cudaError_t launch_pass(const hx_plan_s* plan, const PassCfg& p, uint64_t
     const size_t smem = pass_smem(p);
     PassKernel k = pick(forward, p);
     if (!k) return cudaErrorInvalidConfiguration;
+    MulPassKernel km = nullptr;
+    if (mul_b) {
+        if (forward || p.pipe == 1 || p.logGc != 0) return cudaErrorInvalidConfiguration;
+        km = pick_mul_inv(p.logR, p.K, p.np, p.pipe == 2);
+        if (!km) return cudaErrorInvalidConfiguration;
+    }
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k,
+        cudaError_t e = cudaFuncSetAttribute(km ? (const void*)km : (const void*)k,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if (p.pipe == 1) {
+    if (km) {
+        dim3 grid(tiles * ((n_polys + p.np - 1) / p.np), plan->n_limbs);
+        const uint32_t slot = timing_begin(stream, pass_kernel_id(false, p, true));
+        km<<<grid, threads, smem, stream>>>(a, mul_b, mul_mf);
+        timing_end(slot, stream);
+    } else if (p.pipe == 1) {
         int sms = 0;
         const int per_sm = resident_blocks(k, threads, smem, &sms);
         const uint64_t total = (uint64_t)tiles * n_polys * plan->n_limbs;
@@ -311,6 +325,23 @@ cudaError_t launch_ntt(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+bool mul_fusable(const NttCfg& cfg) {
+    if (is_cluster(cfg)) return false;
+    const PassCfg& p = cfg.pass[cfg.npass - 1];   // the inverse runs this pass first
+    return p.pipe != 1 && p.logGc == 0 && pick_mul_inv(p.logR, p.K, p.np, p.pipe == 2);
+}
+
+cudaError_t launch_mul_inverse(const hx_plan_s* plan, uint64_t* out, const uint64_t* a,
+                               const uint64_t* b, uint32_t n_polys, uint32_t in_mf,
+                               const NttCfg& cfg, cudaStream_t stream) {
+    if (!mul_fusable(cfg)) return cudaErrorNotSupported;
+    const int first = cfg.npass - 1;
+    cudaError_t e = launch_pass(plan, cfg.pass[first], out, a, n_polys, false, cfg.npass == 1, 1,
+                                stream, b, in_mf);
+    if (e != cudaSuccess || cfg.npass == 1) return e;
+    return launch_pass(plan, cfg.pass[0], out, out, n_polys, false, true, 1, stream);
 }
 
 // The fused pass takes the first inverse pass's shape; a schedule with two

@@ -159,6 +159,8 @@ struct TileCtx {
     uint32_t np_valid = 1;      // polynomials of this block's group that exist
     // Cluster-fused transforms (ntt_cluster.cuh): the round that reads its
     // elements from the other phase's layout in the cluster's shared memory.
+    const uint64_t* gin2 = nullptr;   // dyadic product: the second operand (see tile_mul_to_smem)
+    uint32_t mul_mf = 4;              // ... and the input range factor of both operands
     uint32_t xsm = 0;      // shared-window address of this CTA's data tile
     int xK2 = 0;           // row-phase stages (log2 of a row's length)
     int xlogGc = 0;        // log2 of the columns each CTA holds in the column phase
@@ -441,6 +443,41 @@ __device__ __forceinline__ void smem_to_tile(const uint64_t* sm, const TileCtx& 
     }
 }
 
+// The dyadic product of Listing 4 (MultMod with input_mod_factor 1, 2 or 4)
+// as the staging step of the inverse's first pass: the tile of
+// c_i = a_i b_i mod q, a from c.gin and b from c.gin2 (forward outputs below
+// mul_mf q), Barrett-reduced exactly as EltwiseMultMod reduces it, written to
+// shared memory where tile_to_smem would write a.  Both tiles are read with
+// 16-byte loads; the product never goes to HBM.
+template <int K, int LOG_R, int NP = 1>
+__device__ __forceinline__ void tile_mul_to_smem(uint64_t* sm, const TileCtx& c, uint32_t TE,
+                                                 const LimbDev& lc) {
+    constexpr int IT = 1 << (LOG_R - 1);
+    const uint64_t q = lc.q;
+    const Barrett br{q, lc.barrett_k, lc.barrett_qm1};
+    const uint32_t mf = c.mul_mf;
+    for (uint32_t pp = 0; pp < (NP > 1 ? c.np_valid : 1u); ++pp) {
+        const uint64_t off = pp * c.poly_stride + (c.b_base << K);
+        const ulonglong2* A = reinterpret_cast<const ulonglong2*>(c.gin + off);
+        const ulonglong2* B = reinterpret_cast<const ulonglong2*>(c.gin2 + off);
+        uint64_t* smp = sm + pp * padded(TE);
+        ulonglong2 va[IT], vb[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            va[it] = __ldg(A + threadIdx.x + it * c.nthreads);
+            vb[it] = __ldg(B + threadIdx.x + it * c.nthreads);
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const uint32_t l = 2 * (threadIdx.x + it * c.nthreads);
+            smp[pad(l)] = barrett_mulmod(small_mod_rt(va[it].x, q, mf),
+                                         small_mod_rt(vb[it].x, q, mf), br);
+            smp[pad(l) + 1] = barrett_mulmod(small_mod_rt(va[it].y, q, mf),
+                                             small_mod_rt(vb[it].y, q, mf), br);
+        }
+    }
+}
+
 // Executes round I (in execution order) and the ones after it.  COLUMN
 // passes (logGc > 0) read and write HBM directly in their first and last
 // rounds; row passes do so at their low-stage end only (the forward's first
@@ -506,7 +543,8 @@ __host__ __device__ constexpr uint32_t staged_twiddles(int logGb, int K) {
 // map is strided.
 // With TWS the tile's twiddles are first copied to shared memory after the
 // NP data tiles (stage_twiddles), overlapping the first data loads.
-template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false>
+template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false,
+          bool MUL = false>
 __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, const LimbDev& lc,
                                              uint32_t TE) {
     constexpr bool staged_in = !COLUMN && !FWD;
@@ -518,8 +556,12 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
         cp_async_commit();
         tw = tws;
     }
+    static_assert(!MUL || staged_in, "the product stages an inverse row tile");
     if (staged_in) {
-        tile_to_smem<K, LOG_R, NP>(sm, c, TE);
+        if constexpr (MUL)
+            tile_mul_to_smem<K, LOG_R, NP>(sm, c, TE, lc);
+        else
+            tile_to_smem<K, LOG_R, NP>(sm, c, TE);
         if constexpr (TWS) cp_async_wait<0>();
         __syncthreads();
     }
@@ -544,10 +586,16 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
 // within 16 bytes).  Blocks have at most 512 threads, which 512 x 96
 // registers fit.
 #define HX_PASS_MAXNREG __maxnreg__(LOG_R == 4 ? 72 : NP > 1 ? 96 : FWD ? 40 : 48)
+// The product's staging step holds both operands' pairs: 56 with 8 elements
+// and one polynomial a thread (no spills), otherwise as the pass kernels.
+#define HX_MUL_MAXNREG __maxnreg__(LOG_R == 4 ? 72 : NP > 1 ? 96 : 56)
 
-// One block per (tile, group of NP polynomials, limb).
-template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false>
-__global__ void HX_PASS_MAXNREG ntt_pass_kernel(PassArgs a) {
+// One tile of one pass for each of the block's NP polynomials: block
+// (tile, group of NP polynomials, limb).  MUL: the inverse's first pass
+// with the dyadic product computed in its staging step.
+template <bool FWD, bool COLUMN, int LOG_R, int K, int NP, bool TWS, bool MUL>
+__device__ __forceinline__ void ntt_pass_body(const PassArgs& a, const uint64_t* b,
+                                              uint32_t in_mf) {
     extern __shared__ uint64_t sm[];
     const uint32_t limb = a.order ? a.order[blockIdx.y] : blockIdx.y;
     const uint32_t n_groups = (a.n_polys + NP - 1) / NP;
@@ -573,8 +621,27 @@ __global__ void HX_PASS_MAXNREG ntt_pass_kernel(PassArgs a) {
     c.last = a.last != 0;
     c.poly_stride = (uint64_t)a.n_limbs << a.L;
     c.np_valid = min((uint32_t)NP, a.n_polys - poly);
-    process_tile<FWD, COLUMN, LOG_R, K, NP, TWS>(sm, c, lc, TE);
+    if constexpr (MUL) {
+        c.gin2 = b + base;
+        c.mul_mf = in_mf;
+    }
+    process_tile<FWD, COLUMN, LOG_R, K, NP, TWS, MUL>(sm, c, lc, TE);
 }
+
+// One block per (tile, group of NP polynomials, limb).
+template <bool FWD, bool COLUMN, int LOG_R, int K, int NP = 1, bool TWS = false>
+__global__ void HX_PASS_MAXNREG ntt_pass_kernel(PassArgs a) {
+    ntt_pass_body<FWD, COLUMN, LOG_R, K, NP, TWS, false>(a, nullptr, 4);
+}
+
+// The inverse's first (row) pass with the dyadic product of a.in and b
+// (both below in_mf q) computed in its staging step (tile_mul_to_smem).
+template <int LOG_R, int K, int NP, bool TWS>
+__global__ void HX_MUL_MAXNREG ntt_mul_inv_kernel(PassArgs a, const uint64_t* b,
+                                                  uint32_t in_mf) {
+    ntt_pass_body<false, false, LOG_R, K, NP, TWS, true>(a, b, in_mf);
+}
+
 
 // ---------------------------------------------------------------------------
 // Persistent, double-buffered variant.  Each block walks the tiles t =
@@ -808,6 +875,13 @@ __global__ void __maxnreg__(LOG_R == 4 ? 72 : FWD ? 40 : 48) ntt_pipe_kernel(Pas
 }
 
 typedef void (*PassKernel)(PassArgs);
+typedef void (*MulPassKernel)(PassArgs, const uint64_t*, uint32_t);
+
+// ntt_mul.cu / ntt_muls.cu: the inverse's first pass with the dyadic product
+// fused in, twiddles through the read-only cache / staged (nullptr: not in
+// the menu)
+MulPassKernel pick_mul_inv(int logR, int K, int np, bool tws);
+MulPassKernel pick_mul_inv_tws(int logR, int K, int np);
 
 // ntt_fwd.cu / ntt_inv.cu
 // ntt_f1.cu, ntt_f2.cu, ntt_i1.cu, ntt_i2.cu: plain kernels with 1 or 2

@@ -73,9 +73,9 @@ void timing_end(uint32_t slot, cudaStream_t s) {
         cudaEventRecord(g_tm[idx - 1].b, s);
 }
 
-static const char* kKernelNames[5] = {"ntt_pass_kernel", "ntt_pipe_kernel",
+static const char* kKernelNames[6] = {"ntt_pass_kernel", "ntt_pipe_kernel",
                                       "ntt_tensor_inv_kernel", "ntt_cluster_kernel",
-                                      "ntt_cluster_tensor_kernel"};
+                                      "ntt_cluster_tensor_kernel", "ntt_mul_inv_kernel"};
 
 template <int KIND>
 __global__ void __launch_bounds__(256) int_mul_probe_kernel(uint32_t iters, uint32_t a,
@@ -253,7 +253,9 @@ extern "C" int hx_kernel_name(uint32_t kernel, char* buf, uint32_t len) {
     const uint32_t logR = (kernel >> 4) & 7u, K = (kernel >> 7) & 31u;
     const uint32_t np = (kernel >> 12) & 3u, tws = (kernel >> 14) & 1u;
     int w;
-    if (kind == 0)
+    if (kind == 0 && ((kernel >> 15) & 1u))   // the product-fused inverse first pass
+        w = snprintf(buf, len, "%s<%u, %u, %u, %u>", kKernelNames[5], logR, K, np, tws);
+    else if (kind == 0)
         w = snprintf(buf, len, "%s<%u, %u, %u, %u, %u, %u>", kKernelNames[0], fwd, column, logR,
                      K, np, tws);
     else if (kind == 1)

@@ -17,7 +17,7 @@ threads and no polling:
     and a stream slot is free -- requests that arrive while earlier batches
     are still on the GPU join the next batch (continuous batching) -- and
     launches each admitted batch on its own CUDA stream as one ragged call
-    per kind of request (hx_polymul_ragged: five kernels for all the batch's
+    per kind of request (hx_polymul_ragged: four kernels for all the batch's
     products, whatever their mix of N and moduli; hx_ntt_ragged: two for
     its forward and two for its inverse transforms) into workspaces taken
     from the torch allocator, with one upload and one download for host

@@ -1,6 +1,6 @@
 """hx_polymul_ragged: a mixed set of negacyclic products (every N from 2^10
 to 2^17, different modulus sets, several polynomials per item, results
-aliasing an operand or not) in one five-kernel call equals the oracle; the
+aliasing an operand or not) in one four-kernel call equals the oracle; the
 operands are left untouched; a short workspace is refused."""
 import numpy as np
 import pytest

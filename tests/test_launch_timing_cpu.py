@@ -1,6 +1,8 @@
 """Host side of the per-launch timing (no GPU): kernel ids name the kernels
 as CUDA tools print them, nothing is recorded until timing is enabled, and
 the bench's per-kernel slot model adds up to the whole-transform model."""
+import json
+
 import pytest
 
 import bench
@@ -54,3 +56,69 @@ def test_fused_slots_are_butterflies_plus_the_tensor_step():
     assert (mul_w + red_w) * 2 + (2 * mul_w + red_w) + 3 * fma_w == bench.SLOTS_TENSOR_WIDE
     mul_n, red_n, fma_n = 3, 2 + 1, 1 + 2 + 1
     assert (mul_n + red_n) * 2 + (2 * mul_n + red_n) + 3 * fma_n == bench.SLOTS_TENSOR_NARROW
+
+
+def test_operation_count_model_at_the_benchmark_size():
+    """The operation-count roofline at N = 2^16 x 32 mixed limbs: a forward
+    call over 4 polynomials is 16 stages x 32768 butterflies x (21 wide limbs
+    x 10 + 11 narrow x 3) x 4 = 509.6 M operations against 134.2 MB (integer
+    side slower at 20 T/s and 6786.6 GB/s); the fused tensor / first inverse
+    pass (9 stages, 3 outputs) is 215 M operations against 167.8 MB (seven
+    operands read, three outputs written): HBM side slower."""
+    N, moduli = 1 << 16, W.mixed_width_primes(32)
+    assert sum(1 for q in moduli if q < 1 << 30) == 11
+    col = bench.kernel_slots(kid(0, 1, 1, 4, 7), N, moduli, per_butterfly=bench.ops_per_butterfly)
+    row = bench.kernel_slots(kid(0, 1, 0, 3, 9), N, moduli, per_butterfly=bench.ops_per_butterfly)
+    assert col + row == 4 * 16 * 32768 * (21 * 10 + 11 * 3) == 509607936
+    clu = bench.kernel_slots(kid(3, 1, 0, 4, 8, 0) | 8 << 15, N, moduli,
+                             per_butterfly=bench.ops_per_butterfly)
+    assert clu == col + row                      # one cluster launch = the whole transform
+    r = bench.op_roofline(col + row, bench.kernel_bytes(kid(3, 1, 0, 4, 8, 0) | 8 << 15, N, 32),
+                          91.0, 20.0e12, 6786.6)
+    assert r["bound"] == "alu" and abs(r["int_us"] - 25.48) < 0.01
+    assert abs(r["hbm_us"] - 134217728 / 6786.6e3) < 1e-9 and abs(r["frac"] - 25.48 / 91) < 1e-3
+    fused = kid(2, 0, 0, 3, 9, 3)
+    ops = bench.kernel_slots(fused, N, moduli, per_butterfly=bench.ops_per_butterfly)
+    assert ops == 3 * 9 * 32768 * (21 * 10 + 11 * 3) == 214990848
+    nbytes = bench.kernel_bytes(fused, N, 32)
+    assert nbytes == 167772160
+    r = bench.op_roofline(ops, nbytes, 69.61, 20.0e12, 6782.0)
+    assert r["bound"] == "hbm" and abs(r["frac"] - 0.3554) < 1e-3
+    assert abs(r["achieved"] - nbytes / 69.61e-6 / 1e9) < 1e-6 and r["peak"] == 6782.0
+    # the cluster tensor launch: all 16 inverse stages plus N^-1, same bytes
+    ct = kid(3, 0, 0, 4, 8, 1) | 8 << 15
+    assert bench.kernel_bytes(ct, N, 32) == nbytes
+    assert (bench.kernel_slots(ct, N, moduli, per_butterfly=bench.ops_per_butterfly)
+            == 3 * 17 * 32768 * (21 * 10 + 11 * 3))
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    h = bench.kernel_source_hash()
+    assert len(h) == 16 and h == bench.kernel_source_hash()
+    sched = [(0, 8, 0, 3, 4, 0, 1), (8, 8, 1, 0, 3, 0, 1)]
+    key = json.dumps([list(p) for p in sched])
+    monkeypatch.setattr(bench, "TRAFFIC_BYTES", {("forward_call", key, h): 123,
+                                                  ("forward_call", key, "0" * 16): 456})
+    assert bench.traffic_for("forward_call", sched) == 123
+    monkeypatch.setattr(bench, "TRAFFIC_BYTES", {("forward_call", key, "0" * 16): 456})
+    assert bench.traffic_for("forward_call", sched) is None      # other sources: no figure
+    assert bench.traffic_for("forward_call", None) is None
+
+
+def test_forward_inverse_figures():
+    """fwd_inv_figures on the benchmark shape: the slot model over both calls
+    = (4 forward + 3 inverse transforms' slots) / time / peak; the
+    operation count: the forward call is integer-bound (25.5 us at 20 T/s),
+    the three-polynomial inverse too (19.1 + 1.2 us of integer work vs 14.8 us
+    of HBM at 6786.6 GB/s)."""
+    N, moduli = 1 << 16, W.mixed_width_primes(32)
+    f = bench.fwd_inv_figures(N, moduli, 90.0, 85.0, 20.0e12, 6786.6)
+    slots = 4 * sum(bench.imad_slots_per_transform(N, moduli))
+    slots += 3 * (slots // 4 + sum(N // 2 * bench.slots_per_butterfly(q) for q in moduli))
+    assert abs(f["fwd_plus_inv_frac_slots"] - slots / 175e-6 / 20e12) < 1e-9
+    assert 0.3 < f["fwd_plus_inv_frac_slots"] < 0.6
+    ops_f = 4 * 16 * 32768 * (21 * 10 + 11 * 3)
+    ops_i = 3 * 17 * 32768 * (21 * 10 + 11 * 3)
+    assert f["forward_bound"] == f["inverse_bound"] == "alu"
+    assert abs(f["fwd_plus_inv_frac"] - (ops_f + ops_i) / 20e12 / 175e-6) < 1e-9
+    assert abs(f["fwd_plus_inv_pairs_per_s"] - 1e6 / (90 / 128 + 85 / 96)) < 1e-6
