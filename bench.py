@@ -254,12 +254,20 @@ class HexStep:
 
 
 # ------------------------------------------------------------------ ragged batch
-def ragged_report(torch, n_polys=512, reps=5):
+#: the ragged kernels' column-pass stages per log2 N before any tuning
+RAGGED_DEFAULT_SPLITS = {12: 5, 13: 6, 14: 7, 15: 7, 16: 8, 17: 8}
+
+
+def ragged_report(torch, imad_rate=None, hbm_gbs=None, n_polys=512, reps=5):
     """The ragged workload (N ~ U{2^10..2^17}, 1-32 limbs of 30/50/60 bits):
     forward NTT of every polynomial as one graph replay of the persistent
-    ragged kernels, against one plain launch per (polynomial, limb) and one
-    call per polynomial; outputs of all three are compared on the device."""
-    from paper_2103_16400_gb300 import capi
+    ragged kernels -- with the default pass shapes and with the shapes the
+    ragged autotuner picks per N -- against one plain launch per
+    (polynomial, limb) and one call per polynomial; outputs of all are
+    compared on the device.  The tuned batch's roofline fraction is the
+    operation count's (N/2 log2 N butterflies per transform, 10 or 3
+    operations each, against 16 bytes of HBM per coefficient)."""
+    from paper_2103_16400_gb300 import capi, tune as hx_tune
     from paper_2103_16400_gb300.tensors import empty, to_device
     entries = W.ragged_batch(n_polys)
     plans, dins, douts, dref, dref2 = [], [], [], [], []
@@ -270,7 +278,13 @@ def ragged_report(torch, n_polys=512, reps=5):
         douts.append(empty(x.shape))
         dref.append(empty(x.shape))
         dref2.append(empty(x.shape))
-    batch = capi.Batch([(p, i, o, 1) for p, i, o in zip(plans, dins, douts)], 1, 1, 1)
+    items = [(p, i, o, 1) for p, i, o in zip(plans, dins, douts)]
+    for L, k1 in RAGGED_DEFAULT_SPLITS.items():
+        capi.hx_ragged_set_split(L, k1)
+    dfixed = [empty(o.shape) for o in douts]
+    fixed = capi.Batch([(p, i, o, 1) for p, i, o in zip(plans, dins, dfixed)], 1, 1, 1)
+    tuned_splits = hx_tune.tune_ragged(items)    # applied process-wide from here on
+    batch = capi.Batch(items, 1, 1, 1)
     info = batch.info()
     one_limb = {}
     for (N, qs) in entries:
@@ -299,14 +313,25 @@ def ragged_report(torch, n_polys=512, reps=5):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    t_fixed = timed(lambda: fixed.run(st))
     t_batch = timed(lambda: batch.run(st))
     t_limb = timed(per_limb)
     t_poly = timed(per_poly)
-    same = all(torch.equal(a, b) and torch.equal(a, c) for a, b, c in zip(douts, dref, dref2))
+    same = all(torch.equal(a, b) and torch.equal(a, c) and torch.equal(a, d)
+               for a, b, c, d in zip(douts, dref, dref2, dfixed))
     lt = info["limb_transforms"]
+    ops = sum(N // 2 * (N.bit_length() - 1) * ops_per_butterfly(q) for N, qs in entries
+              for q in qs)
+    nbytes = sum(16 * N * len(qs) for N, qs in entries)
+    roof = (op_roofline(ops, nbytes, t_batch * 1e3, imad_rate, hbm_gbs)
+            if imad_rate and hbm_gbs else None)
     return {"workload": f"ragged_{n_polys}_polys_N2^10..2^17_1-32_limbs",
             "limb_transforms": lt, "tiles": info["tiles"], "launches_per_replay": info["launches"],
             "batch_ms": t_batch, "batch_limb_transforms_per_s": lt / (t_batch * 1e-3),
+            "fixed_menu_ms": t_fixed, "tuned_over_fixed_speedup": t_fixed / t_batch,
+            "splits": {"tuned": {L: r["k1"] for L, r in tuned_splits.items()},
+                       "fixed": RAGGED_DEFAULT_SPLITS},
+            "roofline": roof,
             "per_limb_launch_ms": t_limb, "per_limb_limb_transforms_per_s": lt / (t_limb * 1e-3),
             "per_poly_call_ms": t_poly, "per_poly_limb_transforms_per_s": lt / (t_poly * 1e-3),
             "speedup_vs_per_limb": t_limb / t_batch, "bit_exact_equal": bool(same)}
@@ -476,7 +501,7 @@ def _throttled_since(before):
 
 
 def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30,
-                   blocking_wait=True):
+                   blocking_wait=False):
     """Poisson arrivals of polynomial-multiply requests (N uniform over
     {2^12, 2^14, 2^16}, 4-32 limbs of the mixed 30/50/60-bit basis, operands
     uniform mod q and resident in HBM) at each rate: the continuous-batching
@@ -528,13 +553,16 @@ def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30
         t0 = time.perf_counter()
         futs = []
         for r, t in zip(served, arrivals):
-            # sleep until the arrival (the interpreter lock stays free for the
-            # server's threads); requests already due go in at once, each
-            # stamped with its scheduled arrival, so lateness here counts as
-            # latency, exactly as in the one-by-one baseline
+            # sleep until just before the arrival (the interpreter lock stays
+            # free for the server's threads), then spin to it, exactly as the
+            # one-by-one baseline does; requests already due go in at once,
+            # each stamped with its scheduled arrival, so lateness here counts
+            # as latency in both
             wait = t - (time.perf_counter() - t0)
             if wait > 1e-4:
                 time.sleep(wait - 5e-5)
+            while time.perf_counter() - t0 < t:
+                pass
             futs.append(srv.submit(r, arrival=t0 + t))
         for f in futs:
             f.result(timeout=600)
@@ -1129,7 +1157,7 @@ def main():
         line["ntt_rates"] = rates
         report("eltwise", eltwise_report)
     if rank == 0 and not args.no_ragged:
-        report("batched", ragged_report)
+        report("batched", lambda t: ragged_report(t, imad_rate, hbm_gbs))
     if rank == 0 and not args.no_serving:
         report("serving", serving_report)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -265,6 +265,21 @@ int hx_eltwise_fma_mod(uint64_t* d_result, const uint64_t* d_a, const uint64_t* 
  */
 int hx_poly_mul(hx_plan_t plan, uint64_t* d_result, uint64_t* d_a, uint64_t* d_b,
                 uint32_t n_polys, hx_stream_t stream);
+
+/* hx_dyadic_inverse: d_result = InvNTT(d_A . d_B), the second half of the
+ *   paper's Listing 4 on spectra the caller already holds: EltwiseMultMod of
+ *   the forward outputs d_A and d_B (both below input_mod_factor q,
+ *   input_mod_factor 1, 2 or 4; q below 2^62 and 4q below 2^64) followed by
+ *   the inverse NTT to [0, q).  The product runs inside the inverse's first
+ *   pass when the plan's inverse schedule starts with a per-tile row pass,
+ *   else as a separate element-wise pass into d_result first.  All
+ *   [n_polys][plan n_limbs][N]; d_A and d_B are only read; d_result may
+ *   equal d_A or d_B, or be disjoint from both.
+ *   Errors: HX_ERR_NULL, HX_ERR_ALIGN, HX_ERR_ARG, HX_ERR_MOD_FACTOR,
+ *   HX_ERR_OVERLAP, HX_ERR_CUDA. */
+int hx_dyadic_inverse(hx_plan_t plan, uint64_t* d_result, const uint64_t* d_A,
+                      const uint64_t* d_B, uint32_t n_polys, uint32_t input_mod_factor,
+                      hx_stream_t stream);
 int hx_ciphertext_tensor(hx_plan_t plan, uint64_t* d_out0, uint64_t* d_out1, uint64_t* d_out2,
                          uint64_t* d_a0, uint64_t* d_a1, uint64_t* d_b0, uint64_t* d_b1,
                          const uint64_t* h_scalars, const uint64_t* d_e0, const uint64_t* d_e1,
@@ -315,6 +330,17 @@ int hx_dyadic_tensor_fma(uint64_t* d_r0, uint64_t* d_r1, uint64_t* d_r2, const u
  *   Replays on different streams must not overlap in time (they share the
  *   counters).
  * hx_batch_info: transforms, tiles and kernel launches per replay.
+ *
+ * hx_ragged_set_split(log2_n, k1) / hx_ragged_get_split(log2_n, &k1): the
+ *   pass shapes of ragged transforms of N = 2^log2_n (12 <= log2_n <= 17): a
+ *   column pass over the first k1 stages then a row pass over the other
+ *   log2_n - k1, both on 2048-element tiles; k1 in [5, 9] with
+ *   6 <= log2_n - k1 <= 11.  Every split gives the same results (it is the
+ *   knob the autotuner turns -- the paper's "choose by trials", Section
+ *   3.2).  The setting is process-wide and read when the tile lists are
+ *   written: by hx_batch_create (a batch keeps the shapes it was created
+ *   with), hx_batch_run_static, hx_ntt_ragged and hx_polymul_ragged.
+ *   Errors: HX_ERR_ARG (split or log2_n outside the menu), HX_ERR_NULL.
  */
 typedef struct hx_ragged_item {
     hx_plan_t plan;
@@ -324,6 +350,8 @@ typedef struct hx_ragged_item {
     uint32_t reserved;
 } hx_ragged_item;
 
+int hx_ragged_set_split(uint32_t log2_n, uint32_t k1);
+int hx_ragged_get_split(uint32_t log2_n, uint32_t* k1);
 int hx_batch_create(hx_batch_t* out, const hx_ragged_item* h_items, uint32_t n_items,
                     uint32_t direction, uint32_t input_mod_factor, uint32_t output_mod_factor);
 int hx_batch_run(hx_batch_t batch, hx_stream_t stream);

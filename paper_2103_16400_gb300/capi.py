@@ -42,10 +42,13 @@ _SIGS = {
     "hx_eltwise_mult_mod": [VP, VP, VP, U64, P64, U32, U32, U32, VP],
     "hx_eltwise_fma_mod": [VP, VP, P64, VP, U64, P64, U32, U32, U32, VP],
     "hx_poly_mul": [VP, VP, VP, VP, U32, VP],
+    "hx_dyadic_inverse": [VP, VP, VP, VP, U32, U32, VP],
     "hx_ciphertext_tensor": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, VP],
     "hx_tensor_fma_inverse": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, U32, VP],
     "hx_dyadic_tensor_fma": [VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U64, P64, U32, U32,
                              U32, VP],
+    "hx_ragged_set_split": [U32, U32],
+    "hx_ragged_get_split": [U32, ctypes.POINTER(U32)],
     "hx_batch_create": [ctypes.POINTER(VP), VP, U32, U32, U32, U32],
     "hx_batch_run": [VP, VP],
     "hx_batch_info": [VP, P64, P64, ctypes.POINTER(U32)],
@@ -324,6 +327,17 @@ def hx_ntt_ragged(items, workspace, workspace_bytes: int, direction: int = 1,
                                                  workspace_bytes, _stream(stream)))
 
 
+def hx_ragged_set_split(log2_n: int, k1: int):
+    """Column-pass stages of ragged transforms at N = 2^log2_n (process-wide)."""
+    _check("hx_ragged_set_split", load().hx_ragged_set_split(log2_n, k1))
+
+
+def hx_ragged_get_split(log2_n: int) -> int:
+    k = U32()
+    _check("hx_ragged_get_split", load().hx_ragged_get_split(log2_n, ctypes.byref(k)))
+    return k.value
+
+
 class Batch:
     """Owns an hx_batch_t: a ragged set of transforms replayed as one graph.
     items: iterable of (plan, d_in, d_out, n_polys)."""
@@ -422,6 +436,13 @@ def hx_eltwise_fma_mod(result, a, scalars, addend, n: int, moduli, n_polys: int 
 def hx_poly_mul(plan, result, a, b, n_polys: int, stream=None):
     _check("hx_poly_mul", load().hx_poly_mul(_h(plan), ptr(result), ptr(a), ptr(b), n_polys,
                                              _stream(stream)))
+
+
+def hx_dyadic_inverse(plan, result, A, B, n_polys: int, input_mod_factor: int = 4,
+                      stream=None):
+    _check("hx_dyadic_inverse", load().hx_dyadic_inverse(_h(plan), ptr(result), ptr(A), ptr(B),
+                                                         n_polys, input_mod_factor,
+                                                         _stream(stream)))
 
 
 def hx_ciphertext_tensor(plan, out0, out1, out2, a0, a1, b0, b1, scalars, e0, e1, e2,

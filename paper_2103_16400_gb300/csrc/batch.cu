@@ -2,11 +2,13 @@
 // modulus sets run as one persistent kernel per pass, replayed as one CUDA
 // graph.
 //
-// Every transform is cut into tiles of 2048 elements (1024 at N = 2^10) from a
-// fixed menu of pass shapes, one per log2 N:
+// Every transform is cut into tiles of 2048 elements (1024 at N = 2^10), in
+// pass shapes chosen per log2 N from a menu:
 //   N = 2^10, 2^11      one pass over all stages (S10, S11)
-//   N = 2^12 .. 2^17    a column pass over the first K1 stages (C5..C8) and a
-//                       row pass over the last K2 (R7..R9), K1 + K2 = log2 N
+//   N = 2^12 .. 2^17    a column pass over the first K1 stages (C5..C9) and a
+//                       row pass over the last K2 (R6..R11), K1 + K2 = log2 N;
+//                       the split K1 per log2 N is a process-wide setting
+//                       (hx_ragged_set_split) that the autotuner chooses
 // The host writes one 32-byte descriptor per tile (operand and result
 // pointers, the limb's constants, tile index, menu entry); a persistent grid of
 // 256-thread blocks takes tiles from the list through an atomic counter, so
@@ -17,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -36,20 +39,39 @@ struct RagTile {
 };
 static_assert(sizeof(RagTile) == 32, "descriptor is 32 bytes");
 
-enum RagKind : uint8_t { RK_S10 = 0, RK_S11, RK_C5, RK_C6, RK_C7, RK_C8, RK_R7, RK_R8, RK_R9 };
+enum RagKind : uint8_t {
+    RK_S10 = 0, RK_S11, RK_C5, RK_C6, RK_C7, RK_C8, RK_R7, RK_R8, RK_R9,
+    RK_C9, RK_R6, RK_R10, RK_R11
+};
+
+static int col_kind(int K1) { return K1 == 9 ? RK_C9 : RK_C5 + (K1 - 5); }
+static int row_kind(int K2) {
+    return K2 == 6 ? RK_R6 : K2 <= 9 ? RK_R7 + (K2 - 7) : K2 == 10 ? RK_R10 : RK_R11;
+}
+
+// The column-pass stage count K1 per log2 N (the row pass takes the other
+// log2 N - K1), process-wide; the defaults are the shapes measured best on
+// GB300 before the tuner existed.
+static std::atomic<int> g_rag_split[18] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
+                                           5, 6, 7, 7, 8, 8};
+
+// A split is in the menu when both passes fit a 2048-element tile of 256
+// threads: column passes of 5 .. 9 stages (2^(11-K1) >= 4 columns), row
+// passes of 6 .. 11.
+static bool split_ok(int L, int K1) {
+    return L >= 12 && L <= 17 && K1 >= 5 && K1 <= 9 && L - K1 >= 6 && L - K1 <= 11;
+}
 
 // kinds of the first (column or single) and second (row) pass for log2 N
 static void rag_kinds(int L, int* first, int* second) {
-    switch (L) {
-        case 10: *first = RK_S10; *second = -1; break;
-        case 11: *first = RK_S11; *second = -1; break;
-        case 12: *first = RK_C5; *second = RK_R7; break;
-        case 13: *first = RK_C6; *second = RK_R7; break;
-        case 14: *first = RK_C7; *second = RK_R7; break;
-        case 15: *first = RK_C7; *second = RK_R8; break;
-        case 16: *first = RK_C8; *second = RK_R8; break;
-        default: *first = RK_C8; *second = RK_R9; break;   // 17
+    if (L == 10 || L == 11) {
+        *first = L == 10 ? RK_S10 : RK_S11;
+        *second = -1;
+        return;
     }
+    const int K1 = g_rag_split[L].load(std::memory_order_relaxed);
+    *first = col_kind(K1);
+    *second = row_kind(L - K1);
 }
 
 // One tile: geometry from the menu, then the same per-tile code as the plain
@@ -102,8 +124,12 @@ __global__ void __maxnreg__(64) ragged_pass_kernel(const RagTile* __restrict__ t
             case RK_C6: rag_tile<FWD, true, 3, 6>(sm, d); break;
             case RK_C7: rag_tile<FWD, true, 3, 7>(sm, d); break;
             case RK_C8: rag_tile<FWD, true, 3, 8>(sm, d); break;
+            case RK_C9: rag_tile<FWD, true, 3, 9>(sm, d); break;
+            case RK_R6: rag_tile<FWD, false, 3, 6>(sm, d); break;
             case RK_R7: rag_tile<FWD, false, 3, 7>(sm, d); break;
             case RK_R8: rag_tile<FWD, false, 3, 8>(sm, d); break;
+            case RK_R10: rag_tile<FWD, false, 3, 10>(sm, d); break;
+            case RK_R11: rag_tile<FWD, false, 3, 11>(sm, d); break;
             default: rag_tile<FWD, false, 3, 9>(sm, d); break;
         }
         __syncthreads();   // tile finished with shared memory and s_next
@@ -168,8 +194,11 @@ __global__ void __maxnreg__(64) ragged_mul_inv_kernel(const MulRagTile* __restri
         switch (d.kind) {
             case RK_S10: rag_mul_tile<2, 10>(sm, d); break;
             case RK_S11: rag_mul_tile<3, 11>(sm, d); break;
+            case RK_R6: rag_mul_tile<3, 6>(sm, d); break;
             case RK_R7: rag_mul_tile<3, 7>(sm, d); break;
             case RK_R8: rag_mul_tile<3, 8>(sm, d); break;
+            case RK_R10: rag_mul_tile<3, 10>(sm, d); break;
+            case RK_R11: rag_mul_tile<3, 11>(sm, d); break;
             default: rag_mul_tile<3, 9>(sm, d); break;
         }
         __syncthreads();   // tile finished with shared memory and s_next
@@ -237,6 +266,19 @@ static void rag_free(hx_batch_s* b) {
     cudaFree(b->d_tiles);
     cudaFree(b->d_counters);
     delete b;
+}
+
+extern "C" int hx_ragged_set_split(uint32_t log2_n, uint32_t k1) {
+    if (!split_ok((int)log2_n, (int)k1)) return HX_ERR_ARG;
+    g_rag_split[log2_n].store((int)k1, std::memory_order_relaxed);
+    return HX_OK;
+}
+
+extern "C" int hx_ragged_get_split(uint32_t log2_n, uint32_t* k1) {
+    if (!k1) return HX_ERR_NULL;
+    if (log2_n < 12 || log2_n > 17) return HX_ERR_ARG;
+    *k1 = (uint32_t)g_rag_split[log2_n].load(std::memory_order_relaxed);
+    return HX_OK;
 }
 
 extern "C" int hx_batch_create(hx_batch_t* out, const hx_ragged_item* items, uint32_t n_items,

@@ -266,6 +266,25 @@ int hx_poly_mul(hx_plan_t plan, uint64_t* r, uint64_t* a, uint64_t* b, uint32_t 
     return hx_ntt_inverse(plan, r, r, n_polys, 1, 1, stream);
 }
 
+int hx_dyadic_inverse(hx_plan_t plan, uint64_t* r, const uint64_t* A, const uint64_t* B,
+                      uint32_t n_polys, uint32_t in_mf, hx_stream_t stream) {
+    if (!plan || !r || !A || !B) return HX_ERR_NULL;
+    if (!aligned16(r) || !aligned16(A) || !aligned16(B)) return HX_ERR_ALIGN;
+    if (n_polys == 0 || (uint64_t)n_polys * plan->n_limbs > (1ull << 31)) return HX_ERR_ARG;
+    if (!(in_mf == 1 || in_mf == 2 || in_mf == 4)) return HX_ERR_MOD_FACTOR;
+    const uint64_t bytes = (uint64_t)n_polys * plan->n_limbs * plan->N * 8;
+    // the result may be one of the spectra, or disjoint from both
+    if ((r != A && partial_overlap(r, A, bytes)) || (r != B && partial_overlap(r, B, bytes)))
+        return HX_ERR_OVERLAP;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mul_fusable(plan->cfg_inv))
+        return cuda_status(launch_mul_inverse(plan, r, A, B, n_polys, in_mf, plan->cfg_inv, s));
+    int st = cuda_status(launch_eltwise(ELT_MULT, r, A, B, nullptr, plan->N, plan->moduli.data(),
+                                        plan->n_limbs, n_polys, in_mf, s));
+    if (st != HX_OK) return st;
+    return hx_ntt_inverse(plan, r, r, n_polys, 1, 1, stream);
+}
+
 int hx_tensor_fma_inverse(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* o2,
                           const uint64_t* A0, const uint64_t* A1, const uint64_t* B0,
                           const uint64_t* B1, const uint64_t* h_scalars, const uint64_t* e0,

@@ -23,9 +23,18 @@ threads and no polling:
     from the torch allocator, with one upload and one download for host
     operands;
   * the completer thread waits on each launched batch's end event in turn
-    (the wait releases the interpreter lock), completes its requests,
+    (spinning in the driver, or sleeping there with blocking_wait; either
+    wait releases the interpreter lock), completes its requests,
     stamping their latency, returns their budget and stream, and wakes the
     engine for any requests that were waiting for them.
+When the server is idle -- nothing in flight, waiting or queued, and the
+request within the budget -- submit() launches an HBM-resident request on
+the calling thread at once, through the per-request calls on that thread's
+current stream (what a direct call would do, without the ragged call's
+descriptor lists), and the completer waits for it by spinning in the driver
+rather than sleeping: a request alone on an idle GPU is answered about as
+fast as the direct calls would answer it.  Under load, requests queue and
+go out in batches as above.
 Batches on different streams overlap on the GPU.  Plans (and so the twiddle
 tables) are created once per (N, moduli) and stay resident.
 
@@ -57,7 +66,16 @@ class Request:
     the inverse NTT of a (Algorithm GS with N^-1, bit-reversed input).  a, b
     are numpy arrays on the host (the result comes back as a numpy array) or
     int64-typed CUDA tensors resident in HBM (the result is a CUDA tensor
-    view, nothing leaves the device); b is only read by "mul"."""
+    view, nothing leaves the device); b is only read by "mul".
+
+    A resident result is a view of its batch's result tensor, allocated on
+    the stream that ran the batch (a server stream, or the submitting
+    thread's current stream when an idle server launched it there) and
+    complete when the future resolves.  A caller that reads it on another stream should call
+    result.record_stream(that_stream) first, so the caching allocator does
+    not hand the memory out again while that stream still reads it.  The
+    HBM budget covers work in flight: a result is no longer counted once its
+    request completes, however long the caller keeps it."""
     N: int
     moduli: Tuple[int, ...]
     a: object
@@ -105,18 +123,26 @@ class Server:
     the transform, uint64 [limbs][N])."""
 
     def __init__(self, hbm_budget: int = 64 << 30, streams=3,
-                 max_batch: int = 256, device: int = 0, blocking_wait: bool = True):
+                 max_batch: int = 256, device: int = 0, blocking_wait: bool = False,
+                 fast_path: bool = True, poll_us: float = 0.0):
         """streams: how many CUDA streams to create, or the streams to use
         (servers that share streams also share the caching allocator's blocks,
         which the allocator keeps per stream).  blocking_wait: the completer
         sleeps in the driver until a batch's end event fires (a blocking-sync
-        event) instead of spinning a host core on it."""
+        event) instead of spinning a host core on it (the default: the spin
+        answers tens of microseconds sooner; either wait releases the
+        interpreter lock) -- after first polling the event for up to poll_us
+        microseconds (0: no polling).  fast_path:
+        an idle server launches a submitted HBM-resident request on the
+        submitting thread (a batch of one, waited on by spinning)."""
         import torch
         self.torch = torch
         self.device = device
         self.budget = int(hbm_budget)
         self.max_batch = max_batch
         self.blocking_wait = blocking_wait
+        self.fast_path = fast_path
+        self.poll_s = max(0.0, poll_us) * 1e-6
         self._bind_device()
         capi.load()
         if isinstance(streams, int):
@@ -135,15 +161,25 @@ class Server:
         # (marshalling, allocation, the ragged call); complete_ms_max: the
         # longest spent handing one finished batch's results to its futures
         self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "launches": 0,
-                      "launch_ms_max": 0.0, "complete_ms_max": 0.0}
+                      "launch_ms_max": 0.0, "complete_ms_max": 0.0, "fast_path": 0,
+                      "completed_by_polling": 0}
         self._lock = threading.Lock()   # in_use, free_streams, n_inflight, stats; _error vs submit
         self._stop = threading.Event()
         self._threads: List[threading.Thread] = []
         self._error: Optional[BaseException] = None
+        self._queued = 0                         # requests in the inbox
+        self._fast_ws = None                     # the idle path's spectra
+        self._fast_ev = None                     # the idle path's end event
+        self._batch_ws: Dict[Tuple[int, str], object] = {}   # per (stream, kind) workspace
 
     def _bind_device(self):
         """Makes the server's device current in the calling thread."""
         self.torch.cuda.set_device(self.device)
+
+    def _device_scope(self):
+        """The server's device made current for a launch from a client thread
+        (restored afterwards)."""
+        return self.torch.cuda.device(self.device)
 
     # ------------------------------------------------------------ client side
     def plan(self, N: int, moduli: Sequence[int]) -> "capi.Plan":
@@ -165,11 +201,71 @@ class Server:
         if type(req.moduli) is not tuple:
             req.moduli = tuple(int(q) for q in req.moduli)   # the plan table's key form
         req.arrival = time.perf_counter() if arrival is None else arrival
+        sid = None
         with self._lock:
             if self._error is not None:
                 raise RuntimeError("the server stopped after an error") from self._error
-            self.inbox.put(req)
+            if (self.fast_path and self._threads and not self._stop.is_set()
+                    and self.n_inflight == 0 and self._queued == 0 and not self.waiting
+                    and self.free_streams and self.in_use + req.device_bytes <= self.budget):
+                # idle: this request is the next batch; launch it here
+                need = req.device_bytes
+                self.in_use += need
+                self.n_inflight += 1
+                sid = self.free_streams.pop()
+                self.stats["fast_path"] += 1
+            else:
+                self._queued += 1
+                self.inbox.put(req)
+        if sid is not None:
+            self._launch_batch([req], sid, need, on_device=True)
         return req.future
+
+    def _launch_one(self, r: "Request", sid: int, need: int) -> dict:
+        """One HBM-resident request through the per-request calls, the idle
+        path's low-latency form, on the submitting thread's current stream
+        (as a direct call would run; no descriptor lists): a product
+        transforms a and b out of place into a workspace the server keeps,
+        then hx_dyadic_inverse (the product inside the inverse's first pass)
+        writes the result; a transform writes it directly.  Its end event
+        is waited on by spinning in the driver (the interpreter lock is
+        released meanwhile): the request is small and alone on the GPU.
+        Only called with nothing in flight, so the workspace and the event
+        are free."""
+        torch = self.torch
+        stream = torch.cuda.current_stream(self.device)
+        plan = self.plans.get((r.N, r.moduli))
+        if plan is None:
+            plan = self.plan(r.N, r.moduli)
+        words = r.limbs * r.N
+        sh = stream.cuda_stream
+        res = torch.empty(words, dtype=torch.int64, device=f"cuda:{self.device}")
+        if r.op == "mul":
+            ws = self._fast_ws
+            if ws is None or ws.numel() < 2 * words:
+                ws = self._fast_ws = torch.empty(2 * words, dtype=torch.int64,
+                                                 device=f"cuda:{self.device}")
+            wa = ws.data_ptr()
+            wb = wa + 8 * words
+            capi.hx_ntt_forward(plan, wa, r.a, 1, 1, 4, sh)
+            capi.hx_ntt_forward(plan, wb, r.b, 1, 1, 4, sh)
+            capi.hx_dyadic_inverse(plan, res, wa, wb, 1, 4, sh)
+            launches = 3
+        else:
+            (capi.hx_ntt_forward if r.op == "fwd" else capi.hx_ntt_inverse)(
+                plan, res, r.a, 1, 1, 1, sh)
+            launches = 1
+        ev = self._fast_ev
+        if ev is None:
+            ev = self._fast_ev = torch.cuda.Event()
+        ev.record(stream)
+        with self._lock:
+            self.stats["batches"] += 1
+            self.stats["requests"] += 1
+            self.stats["max_batch"] = max(self.stats["max_batch"], 1)
+            self.stats["launches"] += launches
+        return {"reqs": [r], "work": (res, np.array([words], np.int64), None, None, None, None),
+                "event": ev, "sid": sid, "bytes": need}
 
     def start(self) -> "Server":
         self._threads = [threading.Thread(target=self._run, name="hexgpu-serve", daemon=True),
@@ -220,12 +316,21 @@ class Server:
                 except queue.Empty:
                     continue
                 if item is not _WAKE:
-                    self.waiting.append(item)
+                    self._take(item)
+                if self._error is not None:       # a launch on a client thread failed
+                    self._fail(self._error)
+                    return
                 self._drain_inbox()
                 while self._admit_and_launch():
                     self._drain_inbox()
         except BaseException as e:              # surface engine errors to the client
             self._fail(e)
+
+    def _take(self, req: "Request"):
+        """A submitted request moves from the inbox to the FIFO wait list."""
+        with self._lock:
+            self._queued -= 1
+        self.waiting.append(req)
 
     def _drain_inbox(self):
         while True:
@@ -234,7 +339,7 @@ class Server:
             except queue.Empty:
                 return
             if item is not _WAKE:
-                self.waiting.append(item)
+                self._take(item)
 
     def _admit_and_launch(self) -> bool:
         if not self.waiting:
@@ -254,12 +359,27 @@ class Server:
             self.in_use += need
             self.n_inflight += 1
             sid = self.free_streams.pop()
+        self._launch_batch(batch, sid, need)
+        return True
+
+    def _launch_batch(self, batch: List[Request], sid: int, need: int, on_device=False):
+        """Launches an admitted batch (stream `sid` and `need` bytes already
+        reserved) and hands it to the completer.  on_device: called from a
+        client thread, which may have another device current."""
         t = time.perf_counter()
         try:
-            b = self._launch(batch, sid, need)
+            if on_device:
+                with self._device_scope():
+                    if len(batch) == 1 and batch[0].resident:
+                        b = self._launch_one(batch[0], sid, need)
+                    else:
+                        b = self._launch(batch, sid, need)
+            else:
+                b = self._launch(batch, sid, need)
         except BaseException as e:
             # the batch never reached the GPU: fail its requests, give back
-            # its budget and stream, then stop the engine (_run fails the rest)
+            # its budget and stream, then stop the server (the engine fails
+            # the rest; a client thread re-raises to its caller)
             for r in batch:
                 if not r.future.done():
                     r.future.set_exception(e)
@@ -267,12 +387,16 @@ class Server:
                 self.in_use -= need
                 self.n_inflight -= 1
                 self.free_streams.append(sid)
-            raise
+                if on_device and self._error is None:
+                    self._error = e       # later submissions are refused
+            if not on_device:
+                raise
+            self.inbox.put(_WAKE)         # the engine fails what is queued and stops
+            return
         t = (time.perf_counter() - t) * 1e3
         with self._lock:
             self.stats["launch_ms_max"] = max(self.stats["launch_ms_max"], t)
         self.done_q.put(b)
-        return True
 
     def _launch(self, reqs: List[Request], sid: int, need: int) -> dict:
         torch = self.torch
@@ -328,13 +452,13 @@ class Server:
                     arr = capi.polymul_items_array(h, [a_ptr[k] for k in idx],
                                                    [b_ptr[k] for k in idx], res_ptr[idx])
                     wsb = capi.hx_polymul_ragged_workspace(arr)
-                    ws = torch.empty(wsb, dtype=torch.uint8, device=dev_name)
+                    ws = self._workspace(sid, op, wsb, dev_name)
                     capi.hx_polymul_ragged(arr, ws, wsb, stream.cuda_stream)
-                    self._count_launches(5)
+                    self._count_launches(4)
                 else:
                     arr = capi.ragged_items_array(h, [a_ptr[k] for k in idx], res_ptr[idx])
                     wsb = capi.hx_ntt_ragged_workspace(arr)
-                    ws = torch.empty(wsb, dtype=torch.uint8, device=dev_name)
+                    ws = self._workspace(sid, op, wsb, dev_name)
                     capi.hx_ntt_ragged(arr, ws, wsb, 1 if op == "fwd" else 2, 1, 1,
                                        stream.cuda_stream)
                     self._count_launches(2)
@@ -352,6 +476,18 @@ class Server:
         work = (res, sizes, out_host, staged, pinned, workspaces)
         return {"reqs": reqs, "work": work, "event": ev, "sid": sid, "bytes": need}
 
+    def _workspace(self, sid: int, op: str, nbytes: int, dev_name: str):
+        """The workspace of a batch's ragged call of kind `op` on stream
+        `sid`, kept per (stream, kind) and grown on demand: batches on one
+        stream run in order, so the next one may reuse it; a replaced one
+        goes back to the caching allocator's pool of that stream, whose
+        later work runs after the batches that used it."""
+        ws = self._batch_ws.get((sid, op))
+        if ws is None or ws.numel() < nbytes:
+            ws = self._batch_ws[(sid, op)] = self.torch.empty(
+                max(nbytes, 1 << 20), dtype=self.torch.uint8, device=dev_name)
+        return ws
+
     def _count_launches(self, k: int):
         with self._lock:
             self.stats["launches"] += k
@@ -364,7 +500,17 @@ class Server:
             if b is None:
                 return
             try:
-                b["event"].synchronize()
+                ev = b["event"]
+                polled = False
+                if self.poll_s > 0:
+                    # a short batch is often done within a few hundred
+                    # microseconds: poll (yielding the interpreter lock between
+                    # queries) before the blocking wait's sleep-and-wake
+                    deadline = time.perf_counter() + self.poll_s
+                    while not (polled := ev.query()) and time.perf_counter() < deadline:
+                        time.sleep(0)
+                if not polled:
+                    ev.synchronize()
                 now = time.perf_counter()
                 res, sizes, out_host, _, _, _ = b["work"]
                 parts = res.split(sizes.tolist())        # one view per request
@@ -378,20 +524,32 @@ class Server:
                         r.result = hv[lo:hi].reshape(r.limbs, r.N).copy()
                     lo = hi
                     r.done = now
+                # the batch's budget and stream are free before its futures
+                # resolve: a client that submits as soon as it has its result
+                # finds the server idle
+                self._release(b)
+                for r in b["reqs"]:
                     r.future.set_result(r.result)
                 t = (time.perf_counter() - now) * 1e3
                 with self._lock:
                     self.stats["complete_ms_max"] = max(self.stats["complete_ms_max"], t)
+                    self.stats["completed_by_polling"] += polled
             except BaseException as e:
                 self._error = e
+                self._release(b)
                 for r in b["reqs"]:
                     if not r.future.done():
                         r.future.set_exception(e)
-            with self._lock:
-                self.in_use -= b["bytes"]
-                self.free_streams.append(b["sid"])
-                self.n_inflight -= 1
             self.inbox.put(_WAKE)
+
+    def _release(self, b: dict):
+        with self._lock:
+            if b.get("released"):
+                return
+            b["released"] = True
+            self.in_use -= b["bytes"]
+            self.free_streams.append(b["sid"])
+            self.n_inflight -= 1
 
 
 def serve_one_by_one(reqs: Sequence[Request], arrivals: Optional[Sequence[float]] = None,

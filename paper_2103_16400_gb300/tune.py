@@ -363,3 +363,90 @@ def tune_tensor(plan: "capi.Plan", n_ct: int, scalars, iters: int = 5, use_cache
             cache[key] = out
             save_cache(cache)
     return out
+
+
+# ---------------------------------------------------------------- ragged batches
+def ragged_splits(log2_n: int) -> List[int]:
+    """Column-pass stage counts the ragged kernels can run at N = 2^log2_n
+    (2048-element tiles: column passes of 5..9 stages, row passes of 6..11)."""
+    if not 12 <= log2_n <= 17:
+        return []
+    return [k1 for k1 in range(5, 10) if 6 <= log2_n - k1 <= 11]
+
+
+def _ragged_key(log2_n: int, moduli: Sequence[int], transforms: int, device_name: str) -> str:
+    # transforms rounded to a power of two: a batch's time depends on how many
+    # tiles it has, not on the exact count
+    bucket = 1 << max(0, int(transforms).bit_length() - 1)
+    return f"{device_name}|ragged|L={log2_n}|{width_class(moduli)}|T={bucket}"
+
+
+def tune_ragged(items, reps: int = 3, use_cache: bool = True, verbose: bool = False) -> dict:
+    """Pick the column/row split of the ragged kernels per log2 N for a set
+    of ragged items (plan, d_in, d_out, n_polys) -- every N from 2^12 up
+    present among them: for each such N, a forward and an inverse ragged call
+    (hx_ntt_ragged, out of place, in a workspace) over that N's items alone,
+    timed under every split of the menu; the fastest sum wins, is applied
+    (hx_ragged_set_split, process-wide) and cached per (GPU, N, width mix,
+    transform count).  Returns {log2 N: {"k1", "us", "tried"}}.  The item
+    buffers are overwritten (d_out with spectra)."""
+    import torch
+    name = torch.cuda.get_device_name()
+    by_n: Dict[int, list] = {}
+    for it in items:
+        plan = it[0]
+        by_n.setdefault(plan.N.bit_length() - 1, []).append(it)
+    st = torch.cuda.current_stream()
+    out = {}
+    for L, its in sorted(by_n.items()):
+        cands = ragged_splits(L)
+        if not cands:
+            continue
+        moduli = [q for it in its for q in it[0].moduli]
+        transforms = sum(it[0].n_limbs * it[3] for it in its)
+        key = _ragged_key(L, moduli, transforms, name)
+        if use_cache:
+            with _lock:
+                hit = load_cache().get(key)
+            if hit and hit.get("k1") in cands:
+                capi.hx_ragged_set_split(L, hit["k1"])
+                out[L] = dict(hit, cached=True)
+                continue
+        h = [it[0].handle for it in its]
+        din = [capi.ptr(it[1]) for it in its]
+        dout = [capi.ptr(it[2]) for it in its]
+        npol = [it[3] for it in its]
+        arr = capi.ragged_items_array(h, din, dout, npol)
+        back = capi.ragged_items_array(h, dout, dout, npol)
+        keep = capi.hx_ragged_get_split(L)
+        best = None
+        for k1 in cands:
+            capi.hx_ragged_set_split(L, k1)
+            wsb = max(capi.hx_ntt_ragged_workspace(arr), capi.hx_ntt_ragged_workspace(back))
+            ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+
+            def run():
+                capi.hx_ntt_ragged(arr, ws, wsb, 1, 1, 1, st)
+                capi.hx_ntt_ragged(back, ws, wsb, 2, 1, 1, st)
+
+            run()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                run()
+            e1.record(st)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / reps
+            if verbose:
+                print(f"ragged L={L} k1={k1} {us:9.1f} us", file=sys.stderr)
+            if best is None or us < best[0]:
+                best = (us, k1)
+        capi.hx_ragged_set_split(L, best[1] if best else keep)
+        res = {"k1": best[1], "us": best[0], "tried": len(cands)}
+        out[L] = res
+        if use_cache:
+            with _lock:
+                cache = load_cache()
+                cache[key] = res
+                save_cache(cache)
+    return out

@@ -68,3 +68,36 @@ def test_fused_product_saves_a_launch(hexlib):
     # two forward calls of two passes, then the inverse's two passes (with
     # the product inside the first) -- or the element-wise kernel on top
     assert counts == {"fused": 6, "composed": 7}
+
+
+@pytest.mark.parametrize("logN", [12, 14])
+def test_dyadic_inverse(hexlib, logN):
+    """hx_dyadic_inverse(A, B) = InvNTT(A . B) for spectra below 4q (lifted
+    by k q), fused (row-pass first inverse pass) and composed (persistent
+    first pass), into a fresh buffer and onto A itself; A and B untouched
+    otherwise."""
+    N = 1 << logN
+    qs = W.mixed_width_primes(4, widths=(30, 50, 60, 62))
+    seed = W.SEED_BASE + 1240 + logN
+    a = W.poly_batch(seed, 0, 2, qs, N)
+    b = W.poly_batch(seed, 1, 2, qs, N)
+    exp = oracle.poly_mul(a, b, qs)
+    A, B = oracle.ntt_forward(a, qs), oracle.ntt_forward(b, qs)
+    for p in range(2):
+        for l, q in enumerate(qs):
+            A[p, l] = W.lazy_lift(W.stream_key(seed, 5, p, l), A[p, l], q, 4)
+            B[p, l] = W.lazy_lift(W.stream_key(seed, 6, p, l), B[p, l], q, 4)
+    plan = capi.Plan(N, qs)
+    K1, gb = logN // 2, 2 if logN == 12 else 1         # row tiles of 32 threads or more
+    for sched in ([(0, K1, 0, 3, 4, 0, 1), (K1, logN - K1, gb, 0, 3, 0, 1)],
+                  [(0, K1, 0, 3, 4, 0, 1), (K1, logN - K1, gb, 0, 3, 1, 1)]):
+        plan.set_schedule(sched)
+        dA, dB, r = to_device(A), to_device(B), empty(A.shape)
+        capi.hx_dyadic_inverse(plan, r, dA, dB, 2, 4)
+        np.testing.assert_array_equal(to_host(r), exp)
+        np.testing.assert_array_equal(to_host(dA), A)
+        np.testing.assert_array_equal(to_host(dB), B)
+        capi.hx_dyadic_inverse(plan, dA, dA, dB, 2, 4)
+        np.testing.assert_array_equal(to_host(dA), exp)
+    with pytest.raises(capi.HexError):
+        capi.hx_dyadic_inverse(plan, r, dA, dB, 2, 8)        # input_mod_factor 8

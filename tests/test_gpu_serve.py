@@ -141,13 +141,24 @@ def test_launch_failure_fails_its_requests_and_stops_the_server(hexlib, monkeypa
 
     monkeypatch.setattr(capi, "hx_polymul_ragged", broken)
     reqs = make_requests(6, W.SEED_BASE + 13)
-    srv = serve.Server(hbm_budget=8 << 30, streams=1).start()
+    srv = serve.Server(hbm_budget=8 << 30, streams=1, fast_path=False).start()
     futs = [srv.submit(r) for r in reqs]
     for f in futs:
         with pytest.raises(capi.HexError):
             f.result(timeout=60)
     with pytest.raises(RuntimeError):
         srv.submit(clone(reqs)[0])
+    with pytest.raises(capi.HexError):
+        srv.stop()
+    assert srv.in_use == 0 and srv.n_inflight == 0
+    # an idle server launches on the submitting thread: the failure comes
+    # back through that request's future, and later submissions are refused
+    srv = serve.Server(hbm_budget=8 << 30, streams=1).start()
+    f = srv.submit(clone(reqs)[0])
+    with pytest.raises(capi.HexError):
+        f.result(timeout=60)
+    with pytest.raises(RuntimeError):
+        srv.submit(clone(reqs)[1])
     with pytest.raises(capi.HexError):
         srv.stop()
     assert srv.in_use == 0 and srv.n_inflight == 0
@@ -180,3 +191,24 @@ def test_products_and_transforms_in_one_stream_of_requests(hexlib):
     for r, g, src in zip(resident, got[len(reqs):], reqs[:4]):
         f = oracle.ntt_forward if r.op == "fwd" else oracle.ntt_inverse
         np.testing.assert_array_equal(to_host(g), f(src.a[None], src.moduli)[0])
+
+
+def test_idle_server_serves_resident_requests_with_per_request_calls(hexlib):
+    """Requests submitted one at a time to an idle server go out on the
+    submitting thread through the per-request calls (forward transforms into
+    the stream's workspace, hx_dyadic_inverse): same bits as the one-by-one
+    baseline and the oracle, for products and both transforms."""
+    from paper_2103_16400_gb300.tensors import to_device, to_host
+    reqs = make_requests(9, W.SEED_BASE + 19)
+    for k, r in enumerate(reqs):
+        r.op = ("mul", "fwd", "inv")[k % 3]
+    res = [serve.Request(r.N, r.moduli, to_device(r.a), to_device(r.b), op=r.op) for r in reqs]
+    with serve.Server(hbm_budget=8 << 30, streams=2) as srv:
+        got = [to_host(srv.submit(r).result(timeout=120)) for r in res]
+        assert srv.stats["fast_path"] == len(reqs)
+    base = clone(reqs)
+    serve.serve_one_by_one(base)
+    for r, g, b in zip(reqs, got, base):
+        np.testing.assert_array_equal(g, b.result)
+        if r.op == "mul":
+            np.testing.assert_array_equal(g, oracle.poly_mul(r.a[None], r.b[None], r.moduli)[0])

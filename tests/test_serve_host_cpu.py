@@ -3,8 +3,9 @@ step is replaced by a fake (no kernels, no streams, no device) must admit
 requests in FIFO order, batch the ones that arrive while a batch is in
 flight (continuous batching), keep the bytes in flight within the HBM
 budget and the batches in flight within the stream slots, hand every
-request its own slice of its batch's result, and fail cleanly when a launch
-fails."""
+request its own slice of its batch's result, launch on the submitting thread
+when idle, and fail cleanly when a launch fails."""
+import contextlib
 import threading
 import time
 
@@ -25,10 +26,13 @@ class _Done:
         if not self.gate.wait(timeout=30):
             raise TimeoutError("batch never released")
 
+    def query(self):
+        return self.gate.is_set()
+
 
 class FakeServer(serve.Server):
-    def __init__(self, budget, n_streams, hold_first=False, fail=False):
-        super().__init__(hbm_budget=budget, streams=list(range(n_streams)))
+    def __init__(self, budget, n_streams, hold_first=False, fail=False, fast_path=True):
+        super().__init__(hbm_budget=budget, streams=list(range(n_streams)), fast_path=fast_path)
         self.batches = []
         self.max_in_use = 0
         self.max_inflight = 0
@@ -38,6 +42,9 @@ class FakeServer(serve.Server):
 
     def _bind_device(self):
         pass
+
+    def _device_scope(self):
+        return contextlib.nullcontext()
 
     def _launch(self, reqs, sid, need):
         if self.fail:
@@ -107,7 +114,7 @@ def test_oversized_request_is_refused():
 
 
 def test_failed_launch_fails_requests_and_stops():
-    srv = FakeServer(budget=1 << 30, n_streams=2, fail=True).start()
+    srv = FakeServer(budget=1 << 30, n_streams=2, fail=True, fast_path=False).start()
     futs = [srv.submit(request(t)) for t in range(5)]
     for f in futs:
         with pytest.raises(capi.HexError):
@@ -143,3 +150,33 @@ def test_mixed_ops_keep_fifo_order():
         assert (f.result(timeout=10) == t).all()
     srv.stop()
     assert [t for b in srv.batches for t in b] == list(range(12))
+
+
+def test_idle_server_launches_on_the_submitting_thread():
+    """Idle (nothing waiting, a stream free): submit() launches the request
+    itself, so its batch exists when submit returns; while that batch holds
+    the only stream, later requests go through the engine as one batch."""
+    srv = FakeServer(budget=1 << 30, n_streams=1, hold_first=True).start()
+    f0 = srv.submit(request(0))
+    assert srv.batches == [[0]] and srv.stats["fast_path"] == 1
+    later = [srv.submit(request(t)) for t in range(1, 5)]
+    time.sleep(0.05)
+    assert srv.batches == [[0]]                   # the stream is busy: they wait
+    srv.gates[0].set()
+    for t, f in enumerate([f0] + later):
+        assert (f.result(timeout=10) == t).all()
+    srv.stop()
+    assert srv.batches == [[0], [1, 2, 3, 4]] and srv.stats["fast_path"] == 1
+    assert srv.in_use == 0 and srv.n_inflight == 0
+
+
+def test_failed_fast_path_launch_fails_its_request_and_stops():
+    srv = FakeServer(budget=1 << 30, n_streams=2, fail=True).start()
+    f = srv.submit(request(0))                    # idle: launched here, and fails
+    with pytest.raises(capi.HexError):
+        f.result(timeout=10)
+    with pytest.raises(RuntimeError):             # later submissions are refused
+        srv.submit(request(1))
+    with pytest.raises(capi.HexError):
+        srv.stop()
+    assert srv.in_use == 0 and srv.n_inflight == 0
