@@ -378,7 +378,10 @@ int hx_batch_destroy(hx_batch_t batch);
  *
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before any
- * stream capture.  All calls share the one array and it keeps the last
+ * stream capture.  Like the plans' device tables, the cached address
+ * belongs to the device's context as it was at that call: after a device
+ * reset (cudaDeviceReset, or the primary context torn down and made anew)
+ * neither may be used again in this process.  All calls share the one array and it keeps the last
  * call's contents (the counters are re-zeroed on `stream` by each call):
  * calls whose work overlaps on the GPU -- on different streams, or on one
  * device from several host threads without ordering -- race on it. */
