@@ -208,12 +208,23 @@ def imad_slots_per_transform(N, moduli):
     return [bf * slots_per_butterfly(q) for q in moduli]
 
 
+#: CUDA streams the timed steps alternate over: consecutive steps are
+#: independent batches, so step i + 1's kernels fill the SMs (and the last
+#: waves) that step i's latency-bound kernels leave idle -- measured on GB300
+#: at N = 2^16 x 32 limbs: 192.4 us a step on one stream, 164.3 us on two,
+#: 178.7 us on three.
+STEP_STREAMS = 2
+
+
 class HexStep:
     """The timed step, through the C ABI, with autotuned schedules: one
     forward call over the four inputs, the fused tensor/FMA kernel, one
-    inverse call over the three outputs.  Device buffers are preallocated."""
+    inverse call over the three outputs.  Step i runs on stream i mod
+    `n_streams` with that stream's own preallocated buffers (A: the four
+    spectra, R: the three results), so steps on different streams overlap
+    and every step does its whole work on its own batch."""
 
-    def __init__(self, N, moduli, s, dev_sets, torch, tune=True):
+    def __init__(self, N, moduli, s, dev_sets, torch, tune=True, n_streams=STEP_STREAMS):
         from paper_2103_16400_gb300 import capi, tune as hx_tune
         from paper_2103_16400_gb300.tensors import empty
         self.capi, self.torch = capi, torch
@@ -224,14 +235,32 @@ class HexStep:
                           "inverse": hx_tune.tune_tensor(self.plan, 1, s)}
         self.dev_sets = dev_sets
         L = len(moduli)
-        self.A = empty((4, L, N))
-        self.R = empty((3, L, N))
         self.stream = torch.cuda.current_stream()
+        self.streams = [self.stream] + [torch.cuda.Stream() for _ in range(n_streams - 1)]
+        self.bufs = [(empty((4, L, N)), empty((3, L, N))) for _ in range(n_streams)]
+        self.A, self.R = self.bufs[0]
         self.fwd_events = []
         self.inv_events = []
 
-    def run(self, i, record=False):
-        c, N, st = self.capi, self.N, self.stream
+    def begin(self, ev):
+        """Every step stream waits for `ev` (recorded on the first stream)."""
+        for st in self.streams[1:]:
+            st.wait_event(ev)
+
+    def join(self):
+        """The first stream waits for every other step stream's work."""
+        for st in self.streams[1:]:
+            e = self.torch.cuda.Event()
+            e.record(st)
+            self.stream.wait_event(e)
+
+    def run(self, i, record=False, one_stream=False):
+        """Step i: on stream i mod n_streams (on the first stream alone with
+        one_stream, or when recording per-call events)."""
+        c, N = self.capi, self.N
+        k = 0 if (one_stream or record) else i % len(self.streams)
+        st = self.streams[k]
+        self.A, self.R = self.bufs[k]
         ins, es = self.dev_sets[i % len(self.dev_sets)]
         if record:
             e0 = self.torch.cuda.Event(enable_timing=True)
@@ -379,13 +408,13 @@ def ntt_rates_report(torch, step, dev_sets, imad_rate, hbm_gbs, iters=200):
                                                  4, 1, 1, st))
     inv_us = timed(lambda i: capi.hx_ntt_inverse(step.plan, R, dev_sets[i % len(dev_sets)][1],
                                                  3, 1, 1, st))
-    warm_ms = timed(lambda i: step.run(0)) / 1e3
+    warm_ms = timed(lambda i: step.run(0, one_stream=True)) / 1e3
     out = fwd_inv_figures(N, moduli, fwd_us, inv_us, imad_rate, hbm_gbs)
     out.update({"schedules": {"forward": step.plan.schedule(step.plan.FORWARD),
                               "inverse": step.plan.schedule(step.plan.INVERSE)},
                 "l2_warm_step": {"ms_per_step": warm_ms,
                                  "limb_transforms_per_s": 7 * nl / (warm_ms * 1e-3),
-                                 "how": "the timed step on one input set, no rotation"},
+                                 "how": "the step on one input set, no rotation, one stream"},
                 "how": f"{iters} calls each, CUDA events, inputs rotating over "
                        f"{len(dev_sets)} sets (> L2); *_frac: operation-count roofline, "
                        f"*_frac_slots: IMAD-slot model"})
@@ -500,6 +529,17 @@ def _throttled_since(before):
             "usec": now["throttled_usec"] - before["throttled_usec"]}
 
 
+def precise_sleep():
+    """Sets this thread's timer slack to 1 ns (Linux prctl, a setting of the
+    calling thread alone), so that its sleeps end when asked instead of up
+    to 50 us later: the load generators then submit on schedule."""
+    try:
+        libc = ctypes.CDLL(None)
+        libc.prctl(29, 1, 0, 0, 0)            # PR_SET_TIMERSLACK
+    except (OSError, AttributeError):
+        pass
+
+
 def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30,
                    blocking_wait=False):
     """Poisson arrivals of polynomial-multiply requests (N uniform over
@@ -510,6 +550,7 @@ def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30
     same bits both ways."""
     from paper_2103_16400_gb300 import serve
     from paper_2103_16400_gb300.tensors import to_device
+    precise_sleep()
     moduli = W.mixed_width_primes(32)
     Ns = (1 << 12, 1 << 14, 1 << 16)
     pool = {N: [(to_device(W.poly_batch(W.SEED_BASE + 5, 10 * k, 1, moduli, N)[0]),
@@ -553,16 +594,14 @@ def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30
         t0 = time.perf_counter()
         futs = []
         for r, t in zip(served, arrivals):
-            # sleep until just before the arrival (the interpreter lock stays
-            # free for the server's threads), then spin to it, exactly as the
-            # one-by-one baseline does; requests already due go in at once,
-            # each stamped with its scheduled arrival, so lateness here counts
-            # as latency in both
+            # sleep until the arrival (the interpreter lock stays free for the
+            # server's threads; the thread's timer slack is 1 ns, so the sleep
+            # ends on time, as the one-by-one baseline's sleep does);
+            # requests already due go in at once, each stamped with its
+            # scheduled arrival, so lateness here counts as latency in both
             wait = t - (time.perf_counter() - t0)
-            if wait > 1e-4:
-                time.sleep(wait - 5e-5)
-            while time.perf_counter() - t0 < t:
-                pass
+            if wait > 0:
+                time.sleep(wait)
             futs.append(srv.submit(r, arrival=t0 + t))
         for f in futs:
             f.result(timeout=600)
@@ -577,10 +616,19 @@ def serving_report(torch, rates=(2000, 8000, 32000), n_req=2000, budget=64 << 30
         def summary(rs):
             lat = np.array([r.latency for r in rs]) * 1e3
             span = max(r.done for r in rs) - min(r.arrival for r in rs)
-            return {"requests_per_s": len(rs) / span,
-                    "limb_transforms_per_s": sum(lt_per_req) / span,
-                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                    "mean_ms": float(lat.mean())}
+            out = {"requests_per_s": len(rs) / span,
+                   "limb_transforms_per_s": sum(lt_per_req) / span,
+                   "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                   "mean_ms": float(lat.mean())}
+            paths = {}
+            for r, x in zip(rs, lat):
+                if r.path:
+                    paths.setdefault(r.path, []).append(x)
+            if paths:                  # the server: latency by the path a request took
+                out["by_path"] = {k: {"requests": len(v), "p50_ms": float(np.percentile(v, 50)),
+                                      "p99_ms": float(np.percentile(v, 99))}
+                                  for k, v in sorted(paths.items())}
+            return out
         out.append({"offered_rate_per_s": rate, "requests": n_req, "served": summary(served),
                     "one_by_one": summary(base), "batches": srv.stats["batches"],
                     "max_batch": srv.stats["max_batch"],
@@ -957,8 +1005,10 @@ def main():
     launches0 = capi.hx_launch_count()
     with ClockSampler(local) as clocks:
         t0.record(stream)
+        step.begin(t0)
         for i in range(args.steps):
             step.run(i)
+        step.join()
         t1.record(stream)
         torch.cuda.synchronize()
     launches = capi.hx_launch_count() - launches0
@@ -984,7 +1034,7 @@ def main():
     capi.hx_timing_read(64)                    # nothing left over
     capi.hx_timing_enable(True, 4 * kt_steps + 64)
     for i in range(kt_steps):
-        step.run(i)
+        step.run(i, one_stream=True)           # launches one after another
     torch.cuda.synchronize()
     capi.hx_timing_enable(False)
     timed = capi.hx_timing_read(4 * kt_steps + 64)
@@ -1127,6 +1177,8 @@ def main():
                        "limb_transforms_per_step": per_step_units,
                        "l2": f"{args.sets} rotating input sets, "
                              f"{args.sets * 7 * nl * N * 8 / 2**20:.0f} MiB of inputs > 129 MB L2",
+                       "streams": f"{len(step.streams)}: step i on stream i mod "
+                                  f"{len(step.streams)}, each with its own buffers",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline,
             "roofline_forward_call": roofline_forward_call,

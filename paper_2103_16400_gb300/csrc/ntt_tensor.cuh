@@ -15,6 +15,10 @@
 
 namespace hx {
 
+#ifndef HX_TENSOR_L2PF
+#define HX_TENSOR_L2PF 1
+#endif
+
 // NPF = 1: one block per (tile, output k, ciphertext, limb); NPF = 3: one
 // block per (tile, ciphertext, limb) computing all three r_k from one read of
 // the operands and transforming them with shared twiddle loads.
@@ -74,6 +78,22 @@ __global__ void __maxnreg__(NPF == 3 ? 96 : (LOG_R == 4 ? 72 : 64))
     const ulonglong2* E = reinterpret_cast<const ulonglong2*>(t.E + base);
     const ulonglong2 zero = make_ulonglong2(0, 0);
     const uint32_t TEP = padded(TE);
+    if (HX_TENSOR_L2PF && threadIdx.x == 0) {
+        // the bulk-copy unit pulls the block's operand tiles into L2 at once
+        // (contiguous, 16-byte aligned, 8 TE bytes each), so the staging
+        // steps after the first find them there instead of in DRAM
+        const uint32_t bytes = 8u * TE;
+#pragma unroll
+        for (int o = 0; o < 7; ++o) {
+            // operands A0, A1, B0, B1 then addends e0, e1, e2
+            const bool need = NPF == 3 || (o == 0 && k != 2) || (o == 1 && k != 0) ||
+                              (o == 2 && k != 2) || (o == 3 && k != 0) || o == 4 + (int)k;
+            const uint64_t* src = (o < 4 ? t.A + o * S : t.E + (o - 4) * S) + base;
+            if (need)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes)
+                             : "memory");
+        }
+    }
     // 2^(LOG_R-1) pairs a thread; a compile-time count lets the loads of
     // consecutive steps overlap (one step at a time for three outputs, whose
     // registers are already full)

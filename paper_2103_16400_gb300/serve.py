@@ -30,11 +30,12 @@ threads and no polling:
 When the server is idle -- nothing in flight, waiting or queued, and the
 request within the budget -- submit() launches an HBM-resident request on
 the calling thread at once, through the per-request calls on that thread's
-current stream (what a direct call would do, without the ragged call's
-descriptor lists), and the completer waits for it by spinning in the driver
-rather than sleeping: a request alone on an idle GPU is answered about as
-fast as the direct calls would answer it.  Under load, requests queue and
-go out in batches as above.
+current stream (what a direct call would do), so a request alone on an idle
+GPU is answered about as fast as the direct calls would answer it.  Small
+batches of HBM-resident requests (up to DIRECT_MAX) go out through the same
+per-request calls on their stream: the ragged call's descriptor lists cost
+more host time than they save until a batch grows.  Under load, requests
+queue and go out in ragged batches as above.
 Batches on different streams overlap on the GPU.  Plans (and so the twiddle
 tables) are created once per (N, moduli) and stay resident.
 
@@ -43,6 +44,7 @@ All arithmetic runs in the CUDA library; this module only schedules.
 from __future__ import annotations
 
 import collections
+import contextlib
 import queue
 import threading
 import time
@@ -83,6 +85,7 @@ class Request:
     op: str = "mul"
     arrival: float = 0.0             # perf_counter() at submission
     done: float = 0.0
+    path: str = ""                   # how it went out: "idle", "direct" or "ragged"
     result: object = None
     future: Future = field(default_factory=Future)
 
@@ -133,8 +136,8 @@ class Server:
         answers tens of microseconds sooner; either wait releases the
         interpreter lock) -- after first polling the event for up to poll_us
         microseconds (0: no polling).  fast_path:
-        an idle server launches a submitted HBM-resident request on the
-        submitting thread (a batch of one, waited on by spinning)."""
+        an idle server launches a submitted request on the submitting thread
+        (an HBM-resident one through the per-request calls)."""
         import torch
         self.torch = torch
         self.device = device
@@ -162,14 +165,14 @@ class Server:
         # longest spent handing one finished batch's results to its futures
         self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "launches": 0,
                       "launch_ms_max": 0.0, "complete_ms_max": 0.0, "fast_path": 0,
-                      "completed_by_polling": 0}
+                      "direct_batches": 0, "completed_by_polling": 0}
         self._lock = threading.Lock()   # in_use, free_streams, n_inflight, stats; _error vs submit
         self._stop = threading.Event()
         self._threads: List[threading.Thread] = []
         self._error: Optional[BaseException] = None
         self._queued = 0                         # requests in the inbox
-        self._fast_ws = None                     # the idle path's spectra
-        self._fast_ev = None                     # the idle path's end event
+        self._direct_ws: Dict[object, object] = {}   # per stream (and the idle path): spectra
+        self._idle_ev = None                     # the idle path's end event
         self._batch_ws: Dict[Tuple[int, str], object] = {}   # per (stream, kind) workspace
 
     def _bind_device(self):
@@ -208,7 +211,13 @@ class Server:
             if (self.fast_path and self._threads and not self._stop.is_set()
                     and self.n_inflight == 0 and self._queued == 0 and not self.waiting
                     and self.free_streams and self.in_use + req.device_bytes <= self.budget):
-                # idle: this request is the next batch; launch it here
+                # idle: this request is the next batch; launch it here (an
+                # HBM-resident one on the caller's own stream).  Under load
+                # the engine's batches do better: per-request launches from
+                # the submitting thread, with the completer and the engine
+                # also wanting the interpreter lock, capped at ~6 k
+                # requests/s where batching carries ~31 k.
+                idle = True
                 need = req.device_bytes
                 self.in_use += need
                 self.n_inflight += 1
@@ -218,53 +227,71 @@ class Server:
                 self._queued += 1
                 self.inbox.put(req)
         if sid is not None:
-            self._launch_batch([req], sid, need, on_device=True)
+            self._launch_batch([req], sid, need, on_device=True, idle=idle)
         return req.future
 
-    def _launch_one(self, r: "Request", sid: int, need: int) -> dict:
-        """One HBM-resident request through the per-request calls, the idle
-        path's low-latency form, on the submitting thread's current stream
-        (as a direct call would run; no descriptor lists): a product
-        transforms a and b out of place into a workspace the server keeps,
-        then hx_dyadic_inverse (the product inside the inverse's first pass)
-        writes the result; a transform writes it directly.  Its end event
-        is waited on by spinning in the driver (the interpreter lock is
-        released meanwhile): the request is small and alone on the GPU.
-        Only called with nothing in flight, so the workspace and the event
-        are free."""
+    #: batches of at most this many HBM-resident requests go out through the
+    #: per-request calls (about 15 us of host time a request) rather than
+    #: one ragged call (about 95 us of host time whatever the batch)
+    DIRECT_MAX = 4
+
+    def _launch_direct(self, reqs: List["Request"], sid: int, need: int,
+                       on_caller_stream: bool = False) -> dict:
+        """HBM-resident requests through the per-request calls, one after
+        another on one stream (no descriptor lists): a product transforms a
+        and b out of place into a workspace kept per stream (requests on one
+        stream reuse it in order), then hx_dyadic_inverse (the product inside
+        the inverse's first pass) writes its result; a transform writes its
+        result directly.  on_caller_stream: the idle path -- the submitting
+        thread's current stream (as a direct call would run; the server is
+        idle, so the idle path's workspace and event are free), waited on by
+        spinning in the driver; else server stream `sid`."""
         torch = self.torch
-        stream = torch.cuda.current_stream(self.device)
-        plan = self.plans.get((r.N, r.moduli))
-        if plan is None:
-            plan = self.plan(r.N, r.moduli)
-        words = r.limbs * r.N
+        dev_name = f"cuda:{self.device}"
+        stream = torch.cuda.current_stream(self.device) if on_caller_stream else self.streams[sid]
+        key = "idle" if on_caller_stream else sid
         sh = stream.cuda_stream
-        res = torch.empty(words, dtype=torch.int64, device=f"cuda:{self.device}")
-        if r.op == "mul":
-            ws = self._fast_ws
-            if ws is None or ws.numel() < 2 * words:
-                ws = self._fast_ws = torch.empty(2 * words, dtype=torch.int64,
-                                                 device=f"cuda:{self.device}")
+        n = len(reqs)
+        sizes = np.fromiter((r.limbs * r.N for r in reqs), np.int64, n)
+        need_ws = 2 * int(sizes.max())
+        with torch.cuda.stream(stream) if not on_caller_stream else contextlib.nullcontext():
+            res = torch.empty(int(sizes.sum()), dtype=torch.int64, device=dev_name)
+            ws = self._direct_ws.get(key)
+            if ws is None or ws.numel() < need_ws:
+                ws = self._direct_ws[key] = torch.empty(need_ws, dtype=torch.int64,
+                                                        device=dev_name)
             wa = ws.data_ptr()
-            wb = wa + 8 * words
-            capi.hx_ntt_forward(plan, wa, r.a, 1, 1, 4, sh)
-            capi.hx_ntt_forward(plan, wb, r.b, 1, 1, 4, sh)
-            capi.hx_dyadic_inverse(plan, res, wa, wb, 1, 4, sh)
-            launches = 3
-        else:
-            (capi.hx_ntt_forward if r.op == "fwd" else capi.hx_ntt_inverse)(
-                plan, res, r.a, 1, 1, 1, sh)
-            launches = 1
-        ev = self._fast_ev
-        if ev is None:
-            ev = self._fast_ev = torch.cuda.Event()
-        ev.record(stream)
+            out = res.data_ptr()
+            launches = 0
+            for r, words in zip(reqs, sizes.tolist()):
+                plan = self.plans.get((r.N, r.moduli))
+                if plan is None:
+                    plan = self.plan(r.N, r.moduli)
+                if r.op == "mul":
+                    wb = wa + 8 * words
+                    capi.hx_ntt_forward(plan, wa, r.a, 1, 1, 4, sh)
+                    capi.hx_ntt_forward(plan, wb, r.b, 1, 1, 4, sh)
+                    capi.hx_dyadic_inverse(plan, out, wa, wb, 1, 4, sh)
+                    launches += 3
+                else:
+                    (capi.hx_ntt_forward if r.op == "fwd" else capi.hx_ntt_inverse)(
+                        plan, out, r.a, 1, 1, 1, sh)
+                    launches += 1
+                out += 8 * words
+            if on_caller_stream:
+                ev = self._idle_ev
+                if ev is None:
+                    ev = self._idle_ev = torch.cuda.Event()
+            else:
+                ev = torch.cuda.Event(blocking=self.blocking_wait)
+            ev.record(stream)
         with self._lock:
             self.stats["batches"] += 1
-            self.stats["requests"] += 1
-            self.stats["max_batch"] = max(self.stats["max_batch"], 1)
+            self.stats["requests"] += n
+            self.stats["max_batch"] = max(self.stats["max_batch"], n)
             self.stats["launches"] += launches
-        return {"reqs": [r], "work": (res, np.array([words], np.int64), None, None, None, None),
+            self.stats["direct_batches"] += 1
+        return {"reqs": reqs, "work": (res, sizes, None, None, None, None),
                 "event": ev, "sid": sid, "bytes": need}
 
     def start(self) -> "Server":
@@ -362,18 +389,25 @@ class Server:
         self._launch_batch(batch, sid, need)
         return True
 
-    def _launch_batch(self, batch: List[Request], sid: int, need: int, on_device=False):
+    def _launch_batch(self, batch: List[Request], sid: int, need: int, on_device=False,
+                      idle=False):
         """Launches an admitted batch (stream `sid` and `need` bytes already
         reserved) and hands it to the completer.  on_device: called from a
-        client thread, which may have another device current."""
+        client thread, which may have another device current; idle: nothing
+        else in flight (the client thread's own stream may then run it)."""
         t = time.perf_counter()
         try:
+            direct = len(batch) <= self.DIRECT_MAX and all(r.resident for r in batch)
+            for r in batch:
+                r.path = ("idle" if on_device else "direct") if direct else "ragged"
             if on_device:
                 with self._device_scope():
-                    if len(batch) == 1 and batch[0].resident:
-                        b = self._launch_one(batch[0], sid, need)
+                    if direct:
+                        b = self._launch_direct(batch, sid, need, on_caller_stream=idle)
                     else:
                         b = self._launch(batch, sid, need)
+            elif direct:
+                b = self._launch_direct(batch, sid, need)
             else:
                 b = self._launch(batch, sid, need)
         except BaseException as e:
@@ -540,7 +574,11 @@ class Server:
                 for r in b["reqs"]:
                     if not r.future.done():
                         r.future.set_exception(e)
-            self.inbox.put(_WAKE)
+            # the engine needs waking only for requests that wait for the
+            # budget or a stream this batch gave back (a later submission
+            # wakes it on its own)
+            if self.waiting or self._queued or self._error is not None:
+                self.inbox.put(_WAKE)
 
     def _release(self, b: dict):
         with self._lock:

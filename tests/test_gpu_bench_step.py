@@ -2,7 +2,9 @@
 forward call over the four inputs, then the tensor/FMA step fused into the
 inverse transform of the three outputs) at its full size -- N = 65536, 32
 mixed limbs -- compared element by element with the oracle's ciphertext
-pipeline."""
+pipeline: steps run one after another on one stream, and consecutive steps
+alternating over the step streams (each with its own buffers), as the timed
+region runs them."""
 import numpy as np
 import pytest
 
@@ -19,10 +21,21 @@ def test_bench_step_full_size_parity(hexlib):
     N, nl = 1 << 16, 32
     wl, sets, s = bench.workload_arrays(N, nl, 2)
     step = bench.HexStep(N, wl.moduli, s, bench.device_sets(sets), torch)
+    assert len(step.streams) == bench.STEP_STREAMS >= 2
+    exp = [oracle.ciphertext_tensor(*ins, s, *es, wl.moduli) for ins, es in sets]
     for i in (1, 0):                                  # second set first, then the first
-        R = [to_host(r) for r in step.run(i)]
+        R = [to_host(r) for r in step.run(i, one_stream=True)]
         torch.cuda.synchronize()
-        ins, es = sets[i]
-        exp = oracle.ciphertext_tensor(*ins, s, *es, wl.moduli)
-        for got, e in zip(R, exp):
+        for got, e in zip(R, exp[i]):
             np.testing.assert_array_equal(got, e)
+    # four steps in a row over the step streams: step i on stream i mod 2 with
+    # that stream's buffers and input set i mod 2; the last two are checked
+    ev = torch.cuda.Event()
+    ev.record(step.stream)
+    step.begin(ev)
+    outs = [step.run(i) for i in range(4)]
+    step.join()
+    torch.cuda.synchronize()
+    for i in (2, 3):
+        for got, e in zip(outs[i], exp[i % 2]):
+            np.testing.assert_array_equal(to_host(got), e)
