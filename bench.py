@@ -124,7 +124,22 @@ def kernel_source_hash():
 #: hash is not the running build's gives no figure (the field is null), so a
 #: changed kernel never reports stale traffic.  profiles/ records the
 #: capture commands.
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {
+    ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]", "5f7181598bd2d594"):
+        67254272 + 17271808 + 100655104 + 13970944,
+    ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 1]]", "5f7181598bd2d594"):
+        67251968 + 16945664 + 100655872 + 14300416,
+    ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]", "5f7181598bd2d594"):
+        67319040 + 22943744 + 100591360 + 13690112,
+    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
+     "5f7181598bd2d594"): 151367168 + 23173888,
+    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
+     "5f7181598bd2d594"): 151422464 + 23115008,
+    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 1, 0, 3, 0, 2]]",
+     "5f7181598bd2d594"): 151430400 + 23465472,
+    ("ntt_tensor_inv_kernel<3, 8, 0, 3>", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 2]]",
+     "5f7181598bd2d594"): 151339264 + 23264000,
+}
 
 
 def traffic_for(what, sched):
@@ -198,6 +213,21 @@ def op_roofline(ops, nbytes, us, imad_rate, hbm_gbs):
                 "unit": "T IMAD-op/s", "frac": t_int / us, "int_us": t_int, "hbm_us": t_hbm}
     return {"bound": "hbm", "achieved": nbytes / (us * 1e-6) / 1e9, "peak": hbm_gbs,
             "unit": "GB/s", "frac": t_hbm / us, "int_us": t_int, "hbm_us": t_hbm}
+
+
+def step_work(N, moduli):
+    """Algorithmic work of one timed step (forward call over four
+    polynomials; tensor step and inverse over three with N^-1): (operations
+    of the operation count, IMAD slots of the slot model, HBM bytes: the
+    forward reads 4 and writes 4 polynomials, the tensor + inverse call reads
+    the 4 spectra and 3 addends and writes 3 results)."""
+    logn = N.bit_length() - 1
+    nl = len(moduli)
+    ops = (4 * logn + 3 * (logn + 1)) * sum(N // 2 * ops_per_butterfly(q) for q in moduli)
+    slots = ((4 * logn + 3 * (logn + 1)) * sum(N // 2 * slots_per_butterfly(q) for q in moduli)
+             + sum(N * slots_per_tensor_position(q) for q in moduli))
+    nbytes = (8 + 10) * 8 * N * nl
+    return ops, slots, nbytes
 
 
 def imad_slots_per_transform(N, moduli):
@@ -409,7 +439,40 @@ def ntt_rates_report(torch, step, dev_sets, imad_rate, hbm_gbs, iters=200):
     inv_us = timed(lambda i: capi.hx_ntt_inverse(step.plan, R, dev_sets[i % len(dev_sets)][1],
                                                  3, 1, 1, st))
     warm_ms = timed(lambda i: step.run(0, one_stream=True)) / 1e3
+    # forward + inverse pairs alternating over the step streams (pair i on
+    # stream i mod n, each stream with its own output buffers): throughput
+    # of independent pairs, as the timed step runs
+    bufs = [(empty((4, nl, N)), empty((3, nl, N))) for _ in step.streams]
+
+    def pair(i):
+        k = i % len(step.streams)
+        s_k = step.streams[k]
+        o4, o3 = bufs[k]
+        capi.hx_ntt_forward(step.plan, o4, dev_sets[i % len(dev_sets)][0], 4, 1, 1, s_k)
+        capi.hx_ntt_inverse(step.plan, o3, dev_sets[i % len(dev_sets)][1], 3, 1, 1, s_k)
+
+    for i in range(3):
+        pair(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    step.begin(e0)
+    for i in range(iters):
+        pair(i)
+    step.join()
+    e1.record(st)
+    torch.cuda.synchronize()
+    pair_us = e0.elapsed_time(e1) / iters * 1e3
     out = fwd_inv_figures(N, moduli, fwd_us, inv_us, imad_rate, hbm_gbs)
+    two = fwd_inv_figures(N, moduli, pair_us * fwd_us / (fwd_us + inv_us),
+                          pair_us * inv_us / (fwd_us + inv_us), imad_rate, hbm_gbs)
+    out["two_streams"] = {"pair_us": pair_us,
+                          "fwd_plus_inv_frac": two["fwd_plus_inv_frac"],
+                          "fwd_plus_inv_frac_slots": two["fwd_plus_inv_frac_slots"],
+                          "limb_transforms_per_s": 7 * nl / (pair_us * 1e-6),
+                          "how": f"a forward call (4 polynomials) and an inverse call (3) per "
+                                 f"pair, pairs alternating over {len(step.streams)} streams "
+                                 f"with their own buffers, {iters} pairs"}
     out.update({"schedules": {"forward": step.plan.schedule(step.plan.FORWARD),
                               "inverse": step.plan.schedule(step.plan.INVERSE)},
                 "l2_warm_step": {"ms_per_step": warm_ms,
@@ -912,7 +975,12 @@ def run_tensor_inv(args, wl, torch):
     N, nl = args.N, args.limbs
     plan = capi.Plan(N, wl.moduli)
     s = W.scalars(wl.seed, 20, wl.moduli)
-    t = hx_tune.tune_tensor(plan, 1, s, verbose=bool(os.environ.get("HX_TUNE_VERBOSE")))
+    if args.schedule:
+        sched = [tuple(p) for p in json.loads(args.schedule)]
+        plan.set_schedule(sched, plan.INVERSE)
+        t = {"inverse": [list(p) for p in sched]}
+    else:
+        t = hx_tune.tune_tensor(plan, 1, s, verbose=bool(os.environ.get("HX_TUNE_VERBOSE")))
     A = to_device(np.stack([W.poly_batch(wl.seed, k, 1, wl.moduli, N) for k in range(4)]))
     E = to_device(np.stack([W.poly_batch(wl.seed, 10 + k, 1, wl.moduli, N) for k in range(3)]))
     R = empty((3, 1, nl, N))
@@ -967,7 +1035,8 @@ def main():
     ap.add_argument("--tuned", action="store_true",
                     help="--case fwd/inv: apply the autotuned schedule (cached) instead of the default")
     ap.add_argument("--schedule", default=None,
-                    help="--case fwd/inv: JSON list of passes to apply instead (profiling)")
+                    help="--case fwd/inv/tensor_inv: JSON list of passes to apply instead "
+                         "(profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -1096,6 +1165,13 @@ def main():
         k["bound"], k["frac"] = r["bound"], r["frac"]
         k["alg_slots_per_launch"] = kernel_slots(kid, N, wl.moduli)
         k["frac_slots"] = k["alg_slots_per_launch"] / (k["avg_us"] * 1e-6) / imad_rate
+    # the whole step at the timed rate (two streams): its algorithmic work
+    # against the step time, both models
+    s_ops, s_slots, s_bytes = step_work(N, wl.moduli)
+    step_us = total_ms / args.steps * 1e3
+    step_roof = dict(op_roofline(s_ops, s_bytes, step_us, imad_rate, hbm_gbs),
+                     frac_slots=s_slots / (step_us * 1e-6) / imad_rate, step_us=step_us,
+                     alg_ops=s_ops, alg_slots=s_slots, alg_bytes=s_bytes)
     roofline = roofline_forward_call
     if kernels:
         dom_id = max(kernels, key=lambda i: kernels[i]["total_ms"])
@@ -1125,6 +1201,7 @@ def main():
                           "bound": roofline_forward_call["bound"],
                           "frac_slots": roofline_forward_call["slots"]["frac"],
                           "us": fwd_call_ms * 1e3},
+            step=step_roof,
             schedules=roofline_forward_call["schedules"])
 
     # the plain forward and inverse calls on their own: the goal's forward +
@@ -1135,7 +1212,7 @@ def main():
             rates = ntt_rates_report(torch, step, dev_sets, imad_rate, hbm_gbs)
             roofline["fwd_inv"] = {k: rates[k] for k in (
                 "forward_us", "inverse_us", "fwd_plus_inv_pairs_per_s", "fwd_plus_inv_frac",
-                "fwd_plus_inv_frac_slots", "forward_frac", "inverse_frac")}
+                "fwd_plus_inv_frac_slots", "forward_frac", "inverse_frac", "two_streams")}
         except Exception as e:               # noqa: BLE001 -- reported, not hidden
             rates = {"error": f"{type(e).__name__}: {e}"}
         torch.cuda.synchronize()
