@@ -56,3 +56,36 @@ def test_cache_round_trip(tmp_path, monkeypatch):
     assert tune.load_cache() == {"k": entry}
     (tmp_path / "sub" / "cache.json").write_text("{not json")
     assert tune.load_cache() == {}                   # a damaged cache is ignored
+
+
+def test_ragged_split_menu_and_keys():
+    """The ragged kernels' splits: a column pass of 5..9 stages and a row
+    pass of 6..11 on 2048-element tiles, for N = 2^12..2^17 only; cache keys
+    tell apart GPU, N, width mix and transform count (rounded down to a power
+    of two)."""
+    assert tune.ragged_splits(11) == [] and tune.ragged_splits(18) == []
+    for L in range(12, 18):
+        ks = tune.ragged_splits(L)
+        assert ks == [k for k in range(5, 10) if 6 <= L - k <= 11] and ks
+        assert all(2 <= 11 - k <= 6 and 0 <= 11 - (L - k) <= k for k in ks)   # tile shapes
+    assert sum(len(tune.ragged_splits(L)) for L in range(12, 18)) == 23
+    mixed = W.mixed_width_primes(8)
+    k = tune._ragged_key(16, mixed, 100, "GB300")
+    assert k == tune._ragged_key(16, mixed[::-1], 127, "GB300")      # same mix, same bucket
+    assert len({k, tune._ragged_key(15, mixed, 100, "GB300"),
+                tune._ragged_key(16, mixed[:7], 100, "GB300"),
+                tune._ragged_key(16, mixed, 128, "GB300"),
+                tune._ragged_key(16, mixed, 100, "B200")}) == 5
+
+
+def test_cluster_options_fit_the_menu():
+    """Cluster schedules: both phases 6..9 stages, cluster of 2..16 CTAs,
+    8 or 16 elements a thread; every (K1, K2) the library instantiates."""
+    menu = {(6, 8), (7, 7), (8, 6), (6, 9), (7, 8), (8, 7), (9, 6), (7, 9), (8, 8), (9, 7),
+            (8, 9), (9, 8)}
+    for L in range(14, 18):
+        opts = tune.cluster_options(L)
+        assert {(a[1], b[1]) for a, b in opts} == {p for p in menu if sum(p) == L}
+        for a, b in opts:
+            c = b[1] - a[3]
+            assert a[5] == b[5] == 3 and 1 <= c <= 4 and a[1] - b[2] == c
