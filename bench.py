@@ -131,6 +131,12 @@ TRAFFIC_BYTES = {
         67251968 + 16945664 + 100655872 + 14300416,
     ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]", "5f7181598bd2d594"):
         67319040 + 22943744 + 100591360 + 13690112,
+    ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]", "5f7181598bd2d594"):
+        67253504 + 22823424 + 100663808 + 14119424,
+    ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 1]]", "5f7181598bd2d594"):
+        67252736 + 22976000 + 100655616 + 14272000,
+    ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]", "5f7181598bd2d594"):
+        67319296 + 22228224 + 100587520 + 13933824,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
      "5f7181598bd2d594"): 151367168 + 23173888,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",

@@ -122,3 +122,16 @@ def test_forward_inverse_figures():
     assert f["forward_bound"] == f["inverse_bound"] == "alu"
     assert abs(f["fwd_plus_inv_frac"] - (ops_f + ops_i) / 20e12 / 175e-6) < 1e-9
     assert abs(f["fwd_plus_inv_pairs_per_s"] - 1e6 / (90 / 128 + 85 / 96)) < 1e-6
+
+
+def test_step_work():
+    """One step at 2^16 x 32 mixed limbs: 16 forward stages on 4 polynomials
+    and 17 inverse stage-equivalents (N^-1 folded) on 3, 243 operations per
+    butterfly column over the limbs (21 x 10 + 11 x 3); 18 polynomial-sized
+    HBM transfers (8 for the forward, 10 for tensor + inverse)."""
+    N, moduli = 1 << 16, W.mixed_width_primes(32)
+    ops, slots, nbytes = bench.step_work(N, moduli)
+    assert ops == (4 * 16 + 3 * 17) * 32768 * 243
+    assert nbytes == 18 * 8 * N * 32
+    tensor = N * (21 * 175 + 11 * 33)
+    assert slots == (4 * 16 + 3 * 17) * 32768 * (21 * 17 + 11 * 4) + tensor
