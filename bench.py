@@ -87,20 +87,22 @@ def slots_per_butterfly(q):
 
 
 #: IMAD slots of the ciphertext tensor's element-wise step per coefficient
-#: position (three outputs), in the same units.  It takes four modular
-#: products (d1's two summed before one reduction) and three Shoup FMAs.
-#: 64-bit words: a 64x64-bit product is its exact high word (11) and low
-#: word (one full and two low halves, 5); a Barrett reduction (Algorithm
-#: "Barrett Reduction": c3 = high word of c1 k, then d - c3 q mod 2^64) is
-#: 11 + 5; so d0 = d2 = 16 + 16, d1 = 2 * 16 + 16, and an FMA (s a - Q q
-#: with Q the high word of s' a) 5 + 11 + 5: 32 + 48 + 32 + 3 * 21 = 175.
-#: 32-bit words: a product is one full 32x32 (3), a reduction one high half
-#: and one low half (2 + 1), an FMA 1 + 2 + 1: 6 + 9 + 6 + 3 * 4 = 33.
-SLOTS_TENSOR_WIDE, SLOTS_TENSOR_NARROW = 175, 33
+#: position (three outputs), in the same units, as the fused kernels compute
+#: it (tensor_r3): two Shoup products a' = a s (a butterfly's multiply each:
+#: 17, or 21 with the exact quotient), three 128-bit products (four full
+#: 32x32 products each, 12; d1 by Karatsuba) and three Barrett reductions
+#: (the high word of c1 k -- truncated 7, exact 11 -- and the low word of
+#: c3 q, 5).  64-bit words below 2^61: 2 * 17 + 3 * 12 + 3 * (7 + 5) = 106;
+#: at or above 2^61: 2 * 21 + 3 * 12 + 3 * (11 + 5) = 126.  32-bit words: a
+#: Shoup product 4, a product one full 32x32 (3), a reduction one high half
+#: and one low half (2 + 1): 2 * 4 + 3 * 3 + 3 * 3 = 26.
+SLOTS_TENSOR_WIDE_TRUNC, SLOTS_TENSOR_WIDE, SLOTS_TENSOR_NARROW = 106, 126, 26
 
 
 def slots_per_tensor_position(q):
-    return SLOTS_TENSOR_NARROW if q < (1 << 30) else SLOTS_TENSOR_WIDE
+    if q < (1 << 30):
+        return SLOTS_TENSOR_NARROW
+    return SLOTS_TENSOR_WIDE_TRUNC if q < (1 << 61) else SLOTS_TENSOR_WIDE
 
 
 def kernel_source_hash():

@@ -253,4 +253,150 @@ __device__ __forceinline__ uint64_t tensor_r(uint64_t d, uint64_t e, uint64_t s,
     return t >= q ? t - q : t;
 }
 
+
+// ---------------------------------------------------------------- ciphertext tensor, fused form
+// The fused inverse passes compute the same r_k = (d_k s + e_k) mod q with
+// fewer multiplies.  The scalar is applied once to each of a0 and a1
+// (a' = a s mod q, a Shoup product: s is fixed per limb), so that
+//   r0 = a0' b0 + e0,  r2 = a1' b1 + e2,  r1 = a0' b1 + a1' b0 + e1   (mod q)
+// take one Barrett reduction each and no FMA, and d1's two products come
+// from one more: (a0' + a1')(b0 + b1) - a0' b0 - a1' b1, exact in 128 bits
+// (Karatsuba).  Every r_k is returned in [0, q), the value the element-wise
+// tensor (tensor_d, tensor_r) returns.
+struct TensorK {
+    uint64_t q, s, sp;   // modulus, scalar s < q, floor(s 2^64 / q)
+    uint64_t bk;         // Barrett factor floor(2^(63+Q) / q), Q = bitlen(q)
+    uint32_t Qm1;        // Q - 1
+    uint32_t mf;         // input_mod_factor of the operands: 1, 2 or 4
+};
+
+// The 128-bit product a b from four 32x32-bit products (mad.wide):
+// a b = p + 2^32 (a0 b1 + a1 b0) + 2^64 a1 b1 with p = a0 b0; the partial
+// sums u = a0 b1 + hi32(p) and v = a1 b0 + lo32(u) stay below 2^64.
+__device__ __forceinline__ void mul_full64(uint64_t a, uint64_t b, uint64_t& hi, uint64_t& lo) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint64_t p, u, v, r;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a0), "r"(b0));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(u) : "r"(a0), "r"(b1), "l"(p >> 32));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(v) : "r"(a1), "r"(b0), "l"(u & 0xffffffffull));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a1), "r"(b1), "l"(u >> 32));
+    hi = r + (v >> 32);
+    lo = (v << 32) | (p & 0xffffffffull);
+}
+
+// Barrett reduction (Algorithm "Barrett Reduction", L = 63 + Q) of d = (hi,
+// lo) < 2^(63+Q) to [0, q).  The exact high word of c1 k leaves the quotient
+// short by at most 2 (c4 < 3q); the truncated one (TR, q < 2^61) by at most
+// 2 more, so c4 < 5q < 2^64 and three subtractions finish it.
+template <bool TR>
+__device__ __forceinline__ uint64_t barrett_reduce128v(uint64_t hi, uint64_t lo, uint64_t q,
+                                                       uint64_t bk, uint32_t Qm1) {
+    const uint64_t c1 = (lo >> Qm1) | (hi << (64 - Qm1));
+    const uint64_t c3 = TR ? mulhi64_trunc(c1, bk) : mulhi64_wide(c1, bk);
+    uint64_t c4 = lo - c3 * q;
+    if (TR) c4 = c4 >= 4 * q ? c4 - 4 * q : c4;
+    c4 = c4 >= 2 * q ? c4 - 2 * q : c4;
+    return c4 >= q ? c4 - q : c4;
+}
+
+// a s mod q in [0, q) for any a < 2^64: the Shoup product, [0, 2q) with the
+// exact quotient, [0, 4q) with the truncated one (TR), then subtractions.
+template <bool TR>
+__device__ __forceinline__ uint64_t tensor_scale64(uint64_t a, const TensorK& c) {
+    uint64_t r = shoup_lazy64v<TR ? 3 : 2>(a, c.s, c.sp, c.q, 0 - c.q);
+    if (TR) r = r >= 2 * c.q ? r - 2 * c.q : r;
+    return r >= c.q ? r - c.q : r;
+}
+
+__device__ __forceinline__ uint64_t add_mod_q(uint64_t x, uint64_t e, uint64_t q) {
+    const uint64_t t = x + e;   // x, e < q
+    return t >= q ? t - q : t;
+}
+
+// 32-bit words (q < 2^30): s' = floor(s 2^32 / q) = sp >> 32 and
+// k' = floor(2^(31+Q) / q) = bk >> 32 (< 2^32 since q > 2^(Q-1)).  With
+// d < 2^(31+Q) (every d here is below 2 q^2 < 2^(2Q+1) <= 2^(31+Q)) the
+// quotient c3 = hi32((d >> (Q-1)) k') is short by at most 2, as for 64-bit
+// words, and d - c3 q < 3q fits 32 bits.
+__device__ __forceinline__ uint32_t barrett_reduce64n(uint64_t d, uint32_t q, uint32_t k32,
+                                                      uint32_t Qm1) {
+    const uint32_t c3 = __umulhi((uint32_t)(d >> Qm1), k32);
+    uint32_t c4 = (uint32_t)d - c3 * q;
+    c4 = c4 >= 2 * q ? c4 - 2 * q : c4;
+    return c4 >= q ? c4 - q : c4;
+}
+
+__device__ __forceinline__ uint32_t tensor_scale32(uint32_t a, uint32_t s, uint32_t sp32,
+                                                   uint32_t q) {
+    const uint32_t r = shoup_mul_lazy32(a, s, sp32, q);   // [0, 2q) for a < 2^32
+    return r >= q ? r - q : r;
+}
+
+// Wd: 0 = 32-bit words (q < 2^30, operands < 4q < 2^32), 1 = 64-bit words
+// with q < 2^61 (truncated quotients), 2 = 64-bit words, exact quotients.
+// a0, a1, b0, b1 < mf q as the forward transform left them; e_k < q.
+template <int Wd>
+__device__ __forceinline__ void tensor_r3(uint64_t a0, uint64_t a1, uint64_t b0, uint64_t b1,
+                                          uint64_t e0, uint64_t e1, uint64_t e2,
+                                          const TensorK& c, uint64_t& r0, uint64_t& r1,
+                                          uint64_t& r2) {
+    b0 = small_mod_rt(b0, c.q, c.mf);
+    b1 = small_mod_rt(b1, c.q, c.mf);
+    if constexpr (Wd == 0) {
+        const uint32_t q = (uint32_t)c.q, s = (uint32_t)c.s, sp = (uint32_t)(c.sp >> 32);
+        const uint32_t k = (uint32_t)(c.bk >> 32);
+        const uint32_t x0 = tensor_scale32((uint32_t)a0, s, sp, q);
+        const uint32_t x1 = tensor_scale32((uint32_t)a1, s, sp, q);
+        const uint64_t p0 = (uint64_t)x0 * (uint32_t)b0, p2 = (uint64_t)x1 * (uint32_t)b1;
+        const uint64_t p1 = (uint64_t)(x0 + x1) * (uint32_t)(b0 + b1) - p0 - p2;
+        r0 = add_mod_q(barrett_reduce64n(p0, q, k, c.Qm1), e0, q);
+        r1 = add_mod_q(barrett_reduce64n(p1, q, k, c.Qm1), e1, q);
+        r2 = add_mod_q(barrett_reduce64n(p2, q, k, c.Qm1), e2, q);
+    } else {
+        constexpr bool TR = Wd == 1;
+        const uint64_t x0 = tensor_scale64<TR>(a0, c), x1 = tensor_scale64<TR>(a1, c);
+        uint64_t h0, l0, h2, l2, h1, l1;
+        mul_full64(x0, b0, h0, l0);
+        mul_full64(x1, b1, h2, l2);
+        mul_full64(x0 + x1, b0 + b1, h1, l1);   // sums < 2q < 2^63
+        // (h1, l1) -= (h0, l0) + (h2, l2): a0' b1 + a1' b0 < 2 q^2
+        const uint64_t s_lo = l0 + l2;
+        const uint64_t s_hi = h0 + h2 + (s_lo < l0 ? 1 : 0);
+        h1 = h1 - s_hi - (l1 < s_lo ? 1 : 0);
+        l1 = l1 - s_lo;
+        r0 = add_mod_q(barrett_reduce128v<TR>(h0, l0, c.q, c.bk, c.Qm1), e0, c.q);
+        r1 = add_mod_q(barrett_reduce128v<TR>(h1, l1, c.q, c.bk, c.Qm1), e1, c.q);
+        r2 = add_mod_q(barrett_reduce128v<TR>(h2, l2, c.q, c.bk, c.Qm1), e2, c.q);
+    }
+}
+
+// One r_k (k = 0, 1, 2) in the same arithmetic, for kernels that compute a
+// single output: d0 = a0' b0, d2 = a1' b1, d1 = a0' b1 + a1' b0.
+template <int Wd>
+__device__ __forceinline__ uint64_t tensor_rk(uint32_t k, uint64_t a0, uint64_t a1, uint64_t b0,
+                                              uint64_t b1, uint64_t e, const TensorK& c) {
+    const uint64_t a = k == 2 ? a1 : a0;                           // the first product's
+    const uint64_t b = small_mod_rt(k == 0 ? b0 : b1, c.q, c.mf);  // operands
+    const uint64_t bs = small_mod_rt(b0, c.q, c.mf);               // k = 1: a1' b0
+    if constexpr (Wd == 0) {
+        const uint32_t q = (uint32_t)c.q, s = (uint32_t)c.s, sp = (uint32_t)(c.sp >> 32);
+        const uint32_t kk = (uint32_t)(c.bk >> 32);
+        uint64_t d = (uint64_t)tensor_scale32((uint32_t)a, s, sp, q) * (uint32_t)b;
+        if (k == 1) d += (uint64_t)tensor_scale32((uint32_t)a1, s, sp, q) * (uint32_t)bs;
+        return add_mod_q(barrett_reduce64n(d, q, kk, c.Qm1), e, q);
+    } else {
+        constexpr bool TR = Wd == 1;
+        uint64_t h, l;
+        mul_full64(tensor_scale64<TR>(a, c), b, h, l);
+        if (k == 1) {
+            uint64_t h2, l2;
+            mul_full64(tensor_scale64<TR>(a1, c), bs, h2, l2);
+            l += l2;
+            h += h2 + (l < l2 ? 1 : 0);
+        }
+        return add_mod_q(barrett_reduce128v<TR>(h, l, c.q, c.bk, c.Qm1), e, c.q);
+    }
+}
+
 }  // namespace hx

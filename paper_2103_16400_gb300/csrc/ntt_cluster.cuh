@@ -156,11 +156,38 @@ __global__ void HX_CLUSTER_MAXNREG ntt_cluster_kernel(PassArgs a) {
     }
 }
 
+// The CTA's row-phase tile of r_k into shared memory, two elements per
+// step; Wd: the limb's word class (tensor_rk).
+template <int Wd, int LOG_R>
+__device__ __forceinline__ void cluster_tensor_tile(uint64_t* sm, const TensorIn& t,
+                                                    const TensorK& tk, uint64_t base, uint64_t S,
+                                                    uint32_t k, uint32_t nthreads) {
+    const ulonglong2* A0 = reinterpret_cast<const ulonglong2*>(t.A + base);
+    const ulonglong2* A1 = reinterpret_cast<const ulonglong2*>(t.A + S + base);
+    const ulonglong2* B0 = reinterpret_cast<const ulonglong2*>(t.A + 2 * S + base);
+    const ulonglong2* B1 = reinterpret_cast<const ulonglong2*>(t.A + 3 * S + base);
+    const ulonglong2* Ek = reinterpret_cast<const ulonglong2*>(t.E + k * S + base);
+    const ulonglong2 zero = make_ulonglong2(0, 0);
+    const bool need0 = k != 2, need1 = k != 0;
+#pragma unroll 4
+    for (int it = 0; it < (1 << (LOG_R - 1)); ++it) {
+        const uint32_t i = threadIdx.x + it * nthreads;
+        const uint32_t l = 2 * i;   // l even: l and l + 1 share one 16-word row
+        const ulonglong2 x0 = need0 ? __ldg(A0 + i) : zero;
+        const ulonglong2 x1 = need1 ? __ldg(A1 + i) : zero;
+        const ulonglong2 y0 = need0 ? __ldg(B0 + i) : zero;
+        const ulonglong2 y1 = need1 ? __ldg(B1 + i) : zero;
+        const ulonglong2 e = __ldg(Ek + i);
+        sm[pad(l)] = tensor_rk<Wd>(k, x0.x, x1.x, y0.x, y1.x, e.x, tk);
+        sm[pad(l) + 1] = tensor_rk<Wd>(k, x0.y, x1.y, y0.y, y1.y, e.y, tk);
+    }
+}
+
 // The ciphertext tensor fused into the cluster inverse: the row-phase tile of
 // output k is computed in shared memory from the forward outputs A0, A1, B0,
 // B1 (< in_mf q) and the addend e_k (< q), r_k = (d_k s + e_k) mod q with d0 =
 // A0 B0, d1 = A0 B1 + A1 B0, d2 = A1 B1 (the element-wise tensor kernel's
-// arithmetic), then inverse-transformed.  Grid (2^LOG_C 3 n_ct, limbs of
+// values, tensor_rk's arithmetic), then inverse-transformed.  Grid (2^LOG_C 3 n_ct, limbs of
 // the launch): cluster index = 3 ct + k, so the three outputs of one
 // ciphertext run side by side and share the operands through L2.
 template <int LOG_R, int K1, int K2>
@@ -180,35 +207,14 @@ __global__ void HX_CLUSTER_MAXNREG ntt_cluster_tensor_kernel(PassArgs a, TensorI
     cluster_ctx<false, K1, K2>(col, row, a, rank, nullptr, a.out + k * S + rowb, sm,
                                E >> LOG_R);
 
-    const uint64_t q = lc.q;
-    const uint32_t mf = t.in_mf;
-    const Barrett br{q, lc.barrett_k, lc.barrett_qm1};
-    const uint64_t s = t.s[li], sp = t.sp[li];
+    const TensorK tk{lc.q, t.s[li], t.sp[li], lc.barrett_k, lc.barrett_qm1, t.in_mf};
     const uint64_t base = rowb + (row.b_base << K2);   // the CTA's rows are contiguous
-    const ulonglong2* A0 = reinterpret_cast<const ulonglong2*>(t.A + base);
-    const ulonglong2* A1 = reinterpret_cast<const ulonglong2*>(t.A + S + base);
-    const ulonglong2* B0 = reinterpret_cast<const ulonglong2*>(t.A + 2 * S + base);
-    const ulonglong2* B1 = reinterpret_cast<const ulonglong2*>(t.A + 3 * S + base);
-    const ulonglong2* Ek = reinterpret_cast<const ulonglong2*>(t.E + k * S + base);
-    const ulonglong2 zero = make_ulonglong2(0, 0);
-    const bool need0 = k != 2, need1 = k != 0;
-#pragma unroll 4
-    for (int it = 0; it < (1 << (LOG_R - 1)); ++it) {
-        const uint32_t i = threadIdx.x + it * row.nthreads;
-        const uint32_t l = 2 * i;
-        const ulonglong2 x0 = need0 ? __ldg(A0 + i) : zero;
-        const ulonglong2 x1 = need1 ? __ldg(A1 + i) : zero;
-        const ulonglong2 y0 = need0 ? __ldg(B0 + i) : zero;
-        const ulonglong2 y1 = need1 ? __ldg(B1 + i) : zero;
-        const ulonglong2 e = __ldg(Ek + i);
-        sm[pad(l)] = tensor_r(tensor_d(k, small_mod_rt(x0.x, q, mf), small_mod_rt(x1.x, q, mf),
-                                       small_mod_rt(y0.x, q, mf), small_mod_rt(y1.x, q, mf), br),
-                              e.x, s, sp, q);
-        sm[pad(l) + 1] =   // l even: l and l + 1 share one 16-word row
-            tensor_r(tensor_d(k, small_mod_rt(x0.y, q, mf), small_mod_rt(x1.y, q, mf),
-                              small_mod_rt(y0.y, q, mf), small_mod_rt(y1.y, q, mf), br),
-                     e.y, s, sp, q);
-    }
+    if (lc.narrow)
+        cluster_tensor_tile<0, LOG_R>(sm, t, tk, base, S, k, row.nthreads);
+    else if (lc.trunc)
+        cluster_tensor_tile<1, LOG_R>(sm, t, tk, base, S, k, row.nthreads);
+    else
+        cluster_tensor_tile<2, LOG_R>(sm, t, tk, base, S, k, row.nthreads);
     __syncthreads();
     cluster_dispatch<false, LOG_R, K1, K2>(sm, lc, col, row);
 }

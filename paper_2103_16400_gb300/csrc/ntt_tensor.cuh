@@ -5,10 +5,12 @@
 // The inverse's first pass is always a row pass that stages its input tile
 // through shared memory.  Here that staging step computes the tile of
 // r_k = (d_k s + e_k) mod q, d0 = A0 B0, d1 = A0 B1 + A1 B0, d2 = A1 B1,
-// straight from the forward outputs A0, A1, B0, B1 and the addend e_k, with
-// the same arithmetic as the element-wise tensor kernel (tensor_d, tensor_r);
-// the pass then runs its Gentleman-Sande rounds on it unchanged.  The three
-// r_k never go to HBM, and the element-wise kernel's launch disappears.
+// straight from the forward outputs A0, A1, B0, B1 and the addend e_k -- the
+// values the element-wise tensor kernel computes, with fewer multiplies
+// (tensor_r3 / tensor_rk: the scalar applied to a0 and a1 once, d1 by
+// Karatsuba, 32-bit words for q < 2^30); the pass then runs its
+// Gentleman-Sande rounds on it unchanged.  The three r_k never go to HBM,
+// and the element-wise kernel's launch disappears.
 #pragma once
 #include "ntt_kernels.cuh"
 #include "ntt_tensor.h"
@@ -18,6 +20,49 @@ namespace hx {
 #ifndef HX_TENSOR_L2PF
 #define HX_TENSOR_L2PF 1
 #endif
+
+// The tile of r_k, two elements per step (16-byte loads; row passes cover
+// whole rows, so the tile is contiguous from b_base << K), into shared memory
+// for the rounds.  Wd: the limb's word class (tensor_r3).
+template <int Wd, int LOG_R, int K, int NPF>
+__device__ __forceinline__ void tensor_tile_to_smem(uint64_t* sm, const TensorIn& t,
+                                                    const TensorK& tk, uint64_t base,
+                                                    uint64_t S, uint32_t k, uint32_t nthreads,
+                                                    uint32_t TEP) {
+    const ulonglong2* A0 = reinterpret_cast<const ulonglong2*>(t.A + base);
+    const ulonglong2* A1 = reinterpret_cast<const ulonglong2*>(t.A + S + base);
+    const ulonglong2* B0 = reinterpret_cast<const ulonglong2*>(t.A + 2 * S + base);
+    const ulonglong2* B1 = reinterpret_cast<const ulonglong2*>(t.A + 3 * S + base);
+    const ulonglong2* E = reinterpret_cast<const ulonglong2*>(t.E + base);
+    const ulonglong2 zero = make_ulonglong2(0, 0);
+    // 2^(LOG_R-1) pairs a thread; a compile-time count lets the loads of
+    // consecutive steps overlap (one step at a time for three outputs, whose
+    // registers are already full)
+#pragma unroll(NPF == 3 ? 1 : 4)
+    for (int it = 0; it < (1 << (LOG_R - 1)); ++it) {
+        const uint32_t i = threadIdx.x + it * nthreads;
+        const uint32_t l = 2 * i;   // l even: l and l + 1 share one 16-word row
+        if constexpr (NPF == 3) {
+            const ulonglong2 x0 = __ldg(A0 + i), x1 = __ldg(A1 + i);
+            const ulonglong2 y0 = __ldg(B0 + i), y1 = __ldg(B1 + i);
+            const ulonglong2 e0 = __ldg(E + i), e1 = __ldg(E + S / 2 + i),
+                             e2 = __ldg(E + S + i);
+            tensor_r3<Wd>(x0.x, x1.x, y0.x, y1.x, e0.x, e1.x, e2.x, tk, sm[pad(l)],
+                          sm[TEP + pad(l)], sm[2 * TEP + pad(l)]);
+            tensor_r3<Wd>(x0.y, x1.y, y0.y, y1.y, e0.y, e1.y, e2.y, tk, sm[pad(l) + 1],
+                          sm[TEP + pad(l) + 1], sm[2 * TEP + pad(l) + 1]);
+        } else {
+            const bool need0 = k != 2, need1 = k != 0;
+            const ulonglong2 x0 = need0 ? __ldg(A0 + i) : zero;
+            const ulonglong2 x1 = need1 ? __ldg(A1 + i) : zero;
+            const ulonglong2 y0 = need0 ? __ldg(B0 + i) : zero;
+            const ulonglong2 y1 = need1 ? __ldg(B1 + i) : zero;
+            const ulonglong2 e = __ldg(E + k * (S / 2) + i);
+            sm[pad(l)] = tensor_rk<Wd>(k, x0.x, x1.x, y0.x, y1.x, e.x, tk);
+            sm[pad(l) + 1] = tensor_rk<Wd>(k, x0.y, x1.y, y0.y, y1.y, e.y, tk);
+        }
+    }
+}
 
 // NPF = 1: one block per (tile, output k, ciphertext, limb); NPF = 3: one
 // block per (tile, ciphertext, limb) computing all three r_k from one read of
@@ -64,19 +109,8 @@ __global__ void __maxnreg__(NPF == 3 ? 96 : (LOG_R == 4 ? 72 : 64))
         tw = tws;
     }
 
-    // the tile of r_k, two elements per step (16-byte loads; row passes
-    // cover whole rows, so the tile is contiguous from b_base << K)
-    const uint64_t q = lc.q;
-    const uint32_t mf = t.in_mf;
-    const Barrett br{q, lc.barrett_k, lc.barrett_qm1};
-    const uint64_t s = t.s[li], sp = t.sp[li];
+    const TensorK tk{lc.q, t.s[li], t.sp[li], lc.barrett_k, lc.barrett_qm1, t.in_mf};
     const uint64_t base = row + (c.b_base << K);
-    const ulonglong2* A0 = reinterpret_cast<const ulonglong2*>(t.A + base);
-    const ulonglong2* A1 = reinterpret_cast<const ulonglong2*>(t.A + S + base);
-    const ulonglong2* B0 = reinterpret_cast<const ulonglong2*>(t.A + 2 * S + base);
-    const ulonglong2* B1 = reinterpret_cast<const ulonglong2*>(t.A + 3 * S + base);
-    const ulonglong2* E = reinterpret_cast<const ulonglong2*>(t.E + base);
-    const ulonglong2 zero = make_ulonglong2(0, 0);
     const uint32_t TEP = padded(TE);
     if (HX_TENSOR_L2PF && threadIdx.x == 0) {
         // the bulk-copy unit pulls the block's operand tiles into L2 at once
@@ -94,40 +128,22 @@ __global__ void __maxnreg__(NPF == 3 ? 96 : (LOG_R == 4 ? 72 : 64))
                              : "memory");
         }
     }
-    // 2^(LOG_R-1) pairs a thread; a compile-time count lets the loads of
-    // consecutive steps overlap (one step at a time for three outputs, whose
-    // registers are already full)
-#pragma unroll(NPF == 3 ? 1 : 4)
-    for (int it = 0; it < (1 << (LOG_R - 1)); ++it) {
-        const uint32_t i = threadIdx.x + it * c.nthreads;
-        const uint32_t l = 2 * i;
-        const bool need0 = NPF == 3 || k != 2, need1 = NPF == 3 || k != 0;
-        const ulonglong2 x0 = need0 ? __ldg(A0 + i) : zero;
-        const ulonglong2 x1 = need1 ? __ldg(A1 + i) : zero;
-        const ulonglong2 y0 = need0 ? __ldg(B0 + i) : zero;
-        const ulonglong2 y1 = need1 ? __ldg(B1 + i) : zero;
-        const uint64_t a0[2] = {small_mod_rt(x0.x, q, mf), small_mod_rt(x0.y, q, mf)};
-        const uint64_t a1[2] = {small_mod_rt(x1.x, q, mf), small_mod_rt(x1.y, q, mf)};
-        const uint64_t b0[2] = {small_mod_rt(y0.x, q, mf), small_mod_rt(y0.y, q, mf)};
-        const uint64_t b1[2] = {small_mod_rt(y1.x, q, mf), small_mod_rt(y1.y, q, mf)};
-#pragma unroll
-        for (int kk = 0; kk < NPF; ++kk) {
-            const uint32_t kt = NPF == 3 ? kk : k;
-            const ulonglong2 e = __ldg(E + kt * (S / 2) + i);
-            sm[kk * TEP + pad(l)] =   // l even: l and l + 1 share one 16-word row
-                tensor_r(tensor_d(kt, a0[0], a1[0], b0[0], b1[0], br), e.x, s, sp, q);
-            sm[kk * TEP + pad(l) + 1] =
-                tensor_r(tensor_d(kt, a0[1], a1[1], b0[1], b1[1], br), e.y, s, sp, q);
-        }
-    }
-    if constexpr (TWS) cp_async_wait<0>();
-    __syncthreads();
-    if (lc.narrow)
+    if (lc.narrow) {
+        tensor_tile_to_smem<0, LOG_R, K, NPF>(sm, t, tk, base, S, k, c.nthreads, TEP);
+        if constexpr (TWS) cp_async_wait<0>();
+        __syncthreads();
         ntt_rounds<false, false, uint32_t, 0, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
-    else if (lc.trunc)
+    } else if (lc.trunc) {
+        tensor_tile_to_smem<1, LOG_R, K, NPF>(sm, t, tk, base, S, k, c.nthreads, TEP);
+        if constexpr (TWS) cp_async_wait<0>();
+        __syncthreads();
         ntt_rounds<false, false, uint64_t, 1, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
-    else
+    } else {
+        tensor_tile_to_smem<2, LOG_R, K, NPF>(sm, t, tk, base, S, k, c.nthreads, TEP);
+        if constexpr (TWS) cp_async_wait<0>();
+        __syncthreads();
         ntt_rounds<false, false, uint64_t, 0, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
+    }
 }
 
 template <int LOG_R, bool TWS, int NPF>

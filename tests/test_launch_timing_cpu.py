@@ -50,12 +50,16 @@ def test_fused_slots_are_butterflies_plus_the_tensor_step():
     fused = bench.kernel_slots(kid(2, 0, 0, 3, 9, 3), N, moduli)
     plain = bench.kernel_slots(kid(0, 0, 0, 3, 9), N, moduli)
     wide = sum(1 for q in moduli if q >= 1 << 30)
-    assert fused - plain == N * (175 * wide + 33 * (len(moduli) - wide))
-    # the element-wise model from its parts: products, reductions, FMAs
-    mul_w, red_w, fma_w = 11 + 5, 11 + 5, 5 + 11 + 5
-    assert (mul_w + red_w) * 2 + (2 * mul_w + red_w) + 3 * fma_w == bench.SLOTS_TENSOR_WIDE
-    mul_n, red_n, fma_n = 3, 2 + 1, 1 + 2 + 1
-    assert (mul_n + red_n) * 2 + (2 * mul_n + red_n) + 3 * fma_n == bench.SLOTS_TENSOR_NARROW
+    assert all(q < 1 << 61 for q in moduli)
+    assert fused - plain == N * (106 * wide + 26 * (len(moduli) - wide))
+    # the model from its parts: two Shoup products a s (a butterfly's
+    # multiply), three 128-bit products, three Barrett reductions
+    prod, red_t, red_x = 4 * 3, 7 + 5, 11 + 5
+    assert 2 * bench.SLOTS_WIDE_TRUNC + 3 * prod + 3 * red_t == bench.SLOTS_TENSOR_WIDE_TRUNC
+    assert 2 * bench.SLOTS_WIDE + 3 * prod + 3 * red_x == bench.SLOTS_TENSOR_WIDE
+    assert 2 * bench.SLOTS_NARROW + 3 * 3 + 3 * (2 + 1) == bench.SLOTS_TENSOR_NARROW
+    assert [bench.slots_per_tensor_position(q) for q in ((1 << 30) - 35, 1 << 40, 1 << 61)] \
+        == [26, 106, 126]
 
 
 def test_operation_count_model_at_the_benchmark_size():
@@ -133,5 +137,5 @@ def test_step_work():
     ops, slots, nbytes = bench.step_work(N, moduli)
     assert ops == (4 * 16 + 3 * 17) * 32768 * 243
     assert nbytes == 18 * 8 * N * 32
-    tensor = N * (21 * 175 + 11 * 33)
+    tensor = N * (21 * 106 + 11 * 26)
     assert slots == (4 * 16 + 3 * 17) * 32768 * (21 * 17 + 11 * 4) + tensor
