@@ -333,6 +333,22 @@ __device__ __forceinline__ uint32_t tensor_scale32(uint32_t a, uint32_t s, uint3
     return r >= q ? r - q : r;
 }
 
+// a b mod q in [0, q) for a, b < q in the same word classes (the dyadic
+// product of the fused polynomial multiply): a b < q^2 is below 2^(63+Q),
+// and below 2^(31+Q) on 32-bit words.
+template <int Wd>
+__device__ __forceinline__ uint64_t mulmod_fused(uint64_t a, uint64_t b, uint64_t q, uint64_t bk,
+                                                 uint32_t Qm1) {
+    if constexpr (Wd == 0) {
+        return barrett_reduce64n((uint64_t)(uint32_t)a * (uint32_t)b, (uint32_t)q,
+                                 (uint32_t)(bk >> 32), Qm1);
+    } else {
+        uint64_t h, l;
+        mul_full64(a, b, h, l);
+        return barrett_reduce128v<Wd == 1>(h, l, q, bk, Qm1);
+    }
+}
+
 // Wd: 0 = 32-bit words (q < 2^30, operands < 4q < 2^32), 1 = 64-bit words
 // with q < 2^61 (truncated quotients), 2 = 64-bit words, exact quotients.
 // a0, a1, b0, b1 < mf q as the forward transform left them; e_k < q.

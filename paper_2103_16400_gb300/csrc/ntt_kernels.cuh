@@ -445,16 +445,17 @@ __device__ __forceinline__ void smem_to_tile(const uint64_t* sm, const TileCtx& 
 
 // The dyadic product of Listing 4 (MultMod with input_mod_factor 1, 2 or 4)
 // as the staging step of the inverse's first pass: the tile of
-// c_i = a_i b_i mod q, a from c.gin and b from c.gin2 (forward outputs below
-// mul_mf q), Barrett-reduced exactly as EltwiseMultMod reduces it, written to
-// shared memory where tile_to_smem would write a.  Both tiles are read with
-// 16-byte loads; the product never goes to HBM.
-template <int K, int LOG_R, int NP = 1>
+// c_i = a_i b_i mod q in [0, q) -- EltwiseMultMod's value -- a from c.gin and
+// b from c.gin2 (forward outputs below mul_mf q), written to shared memory
+// where tile_to_smem would write a.  Wd: the limb's word class (mulmod_fused:
+// 32-bit words below 2^30, truncated Barrett quotients below 2^61).  Both
+// tiles are read with 16-byte loads; the product never goes to HBM.
+template <int K, int LOG_R, int NP, int Wd>
 __device__ __forceinline__ void tile_mul_to_smem(uint64_t* sm, const TileCtx& c, uint32_t TE,
                                                  const LimbDev& lc) {
     constexpr int IT = 1 << (LOG_R - 1);
-    const uint64_t q = lc.q;
-    const Barrett br{q, lc.barrett_k, lc.barrett_qm1};
+    const uint64_t q = lc.q, bk = lc.barrett_k;
+    const uint32_t Qm1 = lc.barrett_qm1;
     const uint32_t mf = c.mul_mf;
     for (uint32_t pp = 0; pp < (NP > 1 ? c.np_valid : 1u); ++pp) {
         const uint64_t off = pp * c.poly_stride + (c.b_base << K);
@@ -470,10 +471,10 @@ __device__ __forceinline__ void tile_mul_to_smem(uint64_t* sm, const TileCtx& c,
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
             const uint32_t l = 2 * (threadIdx.x + it * c.nthreads);
-            smp[pad(l)] = barrett_mulmod(small_mod_rt(va[it].x, q, mf),
-                                         small_mod_rt(vb[it].x, q, mf), br);
-            smp[pad(l) + 1] = barrett_mulmod(small_mod_rt(va[it].y, q, mf),
-                                             small_mod_rt(vb[it].y, q, mf), br);
+            smp[pad(l)] = mulmod_fused<Wd>(small_mod_rt(va[it].x, q, mf),
+                                           small_mod_rt(vb[it].x, q, mf), q, bk, Qm1);
+            smp[pad(l) + 1] = mulmod_fused<Wd>(small_mod_rt(va[it].y, q, mf),
+                                               small_mod_rt(vb[it].y, q, mf), q, bk, Qm1);
         }
     }
 }
@@ -558,9 +559,14 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
     }
     static_assert(!MUL || staged_in, "the product stages an inverse row tile");
     if (staged_in) {
-        if constexpr (MUL)
-            tile_mul_to_smem<K, LOG_R, NP>(sm, c, TE, lc);
-        else
+        if constexpr (MUL) {
+            if (lc.narrow)
+                tile_mul_to_smem<K, LOG_R, NP, 0>(sm, c, TE, lc);
+            else if (lc.trunc)
+                tile_mul_to_smem<K, LOG_R, NP, 1>(sm, c, TE, lc);
+            else
+                tile_mul_to_smem<K, LOG_R, NP, 2>(sm, c, TE, lc);
+        } else
             tile_to_smem<K, LOG_R, NP>(sm, c, TE);
         if constexpr (TWS) cp_async_wait<0>();
         __syncthreads();

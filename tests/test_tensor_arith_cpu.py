@@ -196,3 +196,21 @@ def test_fused_tensor_step_at_the_largest_operands(q, wd):
         assert tensor_r3(a, a, a, a, e, c, 4, wd) == want
         for k in range(3):
             assert tensor_rk(k, a, a, a, a, e[k], c, 4, wd) == want[k]
+
+
+def mulmod_fused(a, b, c, wd):
+    """The fused polynomial multiply's dyadic product on reduced operands."""
+    assert a < c["q"] and b < c["q"]
+    return barrett32(a * b, c) if wd == 0 else barrett64(a * b, c, wd == 1)
+
+
+@pytest.mark.parametrize("q,wd", CASES)
+def test_fused_dyadic_product_equals_its_definition(q, wd):
+    rng = random.Random(q + 11)
+    c = consts(q, 1)
+    edge = [0, 1, q - 1, q // 2, rng.randrange(q)]
+    for _ in range(5000):
+        a = rng.choice(edge) if rng.random() < 0.2 else rng.randrange(q)
+        b = rng.choice(edge) if rng.random() < 0.2 else rng.randrange(q)
+        assert mulmod_fused(a, b, c, wd) == a * b % q
+    assert mulmod_fused(q - 1, q - 1, c, wd) == 1
