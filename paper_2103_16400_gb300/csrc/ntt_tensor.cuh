@@ -64,16 +64,42 @@ __device__ __forceinline__ void tensor_tile_to_smem(uint64_t* sm, const TensorIn
     }
 }
 
+// The inverse stages on the block's output tiles in shared memory: one
+// output, or three one after another (output kk's tile at sm + kk TEP, its
+// HBM destination kk operands after the first).
+template <typename Wd, int AR, int LOG_R, int K, int NPF, bool TWS>
+__device__ __forceinline__ void tensor_rounds(uint64_t* sm, const ulonglong2* __restrict__ tw,
+                                              const LimbDev& lc, const TileCtx& c, uint64_t S,
+                                              uint32_t TEP) {
+    if constexpr (NPF == 3) {
+#pragma unroll 1
+        for (int kk = 0; kk < 3; ++kk) {
+            TileCtx ck = c;
+            ck.gout = c.gout + kk * S;
+            ck.np_valid = 1;
+            ntt_rounds<false, false, Wd, AR, LOG_R, K, 0, 1, TWS>(sm + kk * TEP, tw, lc, ck);
+        }
+    } else {
+        ntt_rounds<false, false, Wd, AR, LOG_R, K, 0, 1, TWS>(sm, tw, lc, c);
+    }
+}
+
 // NPF = 1: one block per (tile, output k, ciphertext, limb); NPF = 3: one
 // block per (tile, ciphertext, limb) computing all three r_k from one read of
-// the operands and transforming them with shared twiddle loads.
-// Register caps (measured on GB300 at N = 2^16 x 32 limbs): 96 for three
-// outputs a block -- five blocks of 128 threads per SM instead of four; the
-// tensor + inverse call 108.5 -> 103.0 us -- and as the per-tile passes for
-// one output a block.  Blocks have at most 512 threads, which 512 x 96
-// registers fit.
+// the operands, then transforming them one after another (the second and
+// third output's twiddles come from L1).
+// Register caps (measured on GB300 at N = 2^16 x 32 limbs): HX_TENSOR3_MAXNREG
+// for three outputs a block, and as the per-tile passes for one output a
+// block.  Transforming the three outputs together (every twiddle load serving
+// three butterflies) needed 96 registers, five blocks of 128 threads per SM;
+// one output at a time fits 72, seven blocks: the tensor + inverse call
+// 96.4 -> 90.3 us (64: 94.3 us, 56: 96.2 us).  Blocks have at most 512
+// threads.
+#ifndef HX_TENSOR3_MAXNREG
+#define HX_TENSOR3_MAXNREG 72
+#endif
 template <int LOG_R, int K, bool TWS, int NPF>
-__global__ void __maxnreg__(NPF == 3 ? 96 : (LOG_R == 4 ? 72 : 64))
+__global__ void __maxnreg__(NPF == 3 ? HX_TENSOR3_MAXNREG : (LOG_R == 4 ? 72 : 64))
     ntt_tensor_inv_kernel(PassArgs a, TensorIn t) {
     extern __shared__ uint64_t sm[];
     const uint32_t limb = a.order ? a.order[t.limb0 + blockIdx.y] : t.limb0 + blockIdx.y;
@@ -132,17 +158,17 @@ __global__ void __maxnreg__(NPF == 3 ? 96 : (LOG_R == 4 ? 72 : 64))
         tensor_tile_to_smem<0, LOG_R, K, NPF>(sm, t, tk, base, S, k, c.nthreads, TEP);
         if constexpr (TWS) cp_async_wait<0>();
         __syncthreads();
-        ntt_rounds<false, false, uint32_t, 0, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
+        tensor_rounds<uint32_t, 0, LOG_R, K, NPF, TWS>(sm, tw, lc, c, S, TEP);
     } else if (lc.trunc) {
         tensor_tile_to_smem<1, LOG_R, K, NPF>(sm, t, tk, base, S, k, c.nthreads, TEP);
         if constexpr (TWS) cp_async_wait<0>();
         __syncthreads();
-        ntt_rounds<false, false, uint64_t, 1, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
+        tensor_rounds<uint64_t, 1, LOG_R, K, NPF, TWS>(sm, tw, lc, c, S, TEP);
     } else {
         tensor_tile_to_smem<2, LOG_R, K, NPF>(sm, t, tk, base, S, k, c.nthreads, TEP);
         if constexpr (TWS) cp_async_wait<0>();
         __syncthreads();
-        ntt_rounds<false, false, uint64_t, 0, LOG_R, K, 0, NPF, TWS>(sm, tw, lc, c);
+        tensor_rounds<uint64_t, 0, LOG_R, K, NPF, TWS>(sm, tw, lc, c, S, TEP);
     }
 }
 
