@@ -538,6 +538,32 @@ __host__ __device__ constexpr uint32_t staged_twiddles(int logGb, int K) {
     return ((1u << K) - 1) << logGb;
 }
 
+// The rounds of one tile for the block's NP polynomials.  A staged row pass
+// of the inverse (its tiles already in shared memory) transforms them one
+// after another when HX_INV_NP_SEQ is set: each polynomial's elements then
+// fit the registers of one (the second polynomial's twiddle loads hit L1),
+// where transforming them together shares every twiddle load but holds NP
+// times the elements.
+#ifndef HX_INV_NP_SEQ
+#define HX_INV_NP_SEQ 1
+#endif
+template <bool FWD, bool COLUMN, typename Wd, int AR, int LOG_R, int K, int NP, bool TWS>
+__device__ __forceinline__ void pass_rounds(uint64_t* sm, const ulonglong2* __restrict__ tw,
+                                            const LimbDev& lc, const TileCtx& c, uint32_t TE) {
+    if constexpr (!FWD && !COLUMN && NP > 1 && HX_INV_NP_SEQ) {
+        TileCtx cp = c;
+        cp.np_valid = 1;
+        const uint32_t n = c.np_valid, step = padded(TE);
+#pragma unroll 1
+        for (uint32_t pp = 0; pp < n; ++pp) {
+            ntt_rounds<FWD, COLUMN, Wd, AR, LOG_R, K, 0, 1, TWS>(sm + pp * step, tw, lc, cp);
+            cp.gout += cp.poly_stride;
+        }
+    } else {
+        ntt_rounds<FWD, COLUMN, Wd, AR, LOG_R, K, 0, NP, TWS>(sm, tw, lc, c);
+    }
+}
+
 // One tile of one pass (for each of NP polynomials), by the whole block
 // (TE >> LOG_R threads): stage in through shared memory where the first
 // round's map is strided, run the rounds, stage out where the last round's
@@ -572,11 +598,11 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
         __syncthreads();
     }
     if (lc.narrow)
-        ntt_rounds<FWD, COLUMN, uint32_t, 0, LOG_R, K, 0, NP, TWS>(sm, tw, lc, c);
+        pass_rounds<FWD, COLUMN, uint32_t, 0, LOG_R, K, NP, TWS>(sm, tw, lc, c, TE);
     else if (lc.trunc)
-        ntt_rounds<FWD, COLUMN, uint64_t, 1, LOG_R, K, 0, NP, TWS>(sm, tw, lc, c);
+        pass_rounds<FWD, COLUMN, uint64_t, 1, LOG_R, K, NP, TWS>(sm, tw, lc, c, TE);
     else
-        ntt_rounds<FWD, COLUMN, uint64_t, 0, LOG_R, K, 0, NP, TWS>(sm, tw, lc, c);
+        pass_rounds<FWD, COLUMN, uint64_t, 0, LOG_R, K, NP, TWS>(sm, tw, lc, c, TE);
     if (staged_out) {
         __syncthreads();
         smem_to_tile<K, LOG_R, NP>(sm, c, TE);
@@ -588,13 +614,23 @@ __device__ __forceinline__ void process_tile(uint64_t* sm, const TileCtx& c, con
 // than the latency of the loads needs): 72 with 16 elements a thread (it
 // would take up to 102: forward call 104 -> 92 us under the schedule with a
 // 7-stage column pass); with 8, 40 in the forward (92 -> 90 us) and 48 in
-// the inverse (80 -> 74 us); 96 with two polynomials a thread (spills stay
-// within 16 bytes).  Blocks have at most 512 threads, which 512 x 96
-// registers fit.
-#define HX_PASS_MAXNREG __maxnreg__(LOG_R == 4 ? 72 : NP > 1 ? 96 : FWD ? 40 : 48)
+// the inverse (80 -> 74 us); 96 with two polynomials a thread in the forward
+// (spills stay within 16 bytes); HX_INV_NP_MAXNREG with two in the
+// inverse's row passes, which transform them one after another
+// (pass_rounds).  Blocks have at
+// most 512 threads, which 512 x 96 registers fit.
+#ifndef HX_INV_NP_MAXNREG
+#define HX_INV_NP_MAXNREG 64
+#endif
+#define HX_PASS_MAXNREG                                                                     \
+    __maxnreg__(LOG_R == 4 ? 72                                                             \
+                : NP > 1   ? (FWD || COLUMN || !HX_INV_NP_SEQ ? 96 : HX_INV_NP_MAXNREG) \
+                : FWD      ? 40                                                             \
+                           : 48)
 // The product's staging step holds both operands' pairs: 56 with 8 elements
-// and one polynomial a thread (no spills), otherwise as the pass kernels.
-#define HX_MUL_MAXNREG __maxnreg__(LOG_R == 4 ? 72 : NP > 1 ? 96 : 56)
+// a thread (no spills); with two polynomials a thread (staged one at a time,
+// transformed one after another) as the inverse's row passes.
+#define HX_MUL_MAXNREG __maxnreg__(LOG_R == 4 ? 72 : NP > 1 ? HX_INV_NP_MAXNREG : 56)
 
 // One tile of one pass for each of the block's NP polynomials: block
 // (tile, group of NP polynomials, limb).  MUL: the inverse's first pass
