@@ -127,26 +127,24 @@ def kernel_source_hash():
 #: changed kernel never reports stale traffic.  profiles/ records the
 #: capture commands.
 TRAFFIC_BYTES = {
-    ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]", "5f7181598bd2d594"):
-        67254272 + 17271808 + 100655104 + 13970944,
-    ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 1]]", "5f7181598bd2d594"):
-        67251968 + 16945664 + 100655872 + 14300416,
-    ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]", "5f7181598bd2d594"):
-        67319040 + 22943744 + 100591360 + 13690112,
-    ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]", "5f7181598bd2d594"):
-        67253504 + 22823424 + 100663808 + 14119424,
-    ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 1]]", "5f7181598bd2d594"):
-        67252736 + 22976000 + 100655616 + 14272000,
-    ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]", "5f7181598bd2d594"):
-        67319296 + 22228224 + 100587520 + 13933824,
+    ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]",
+     "cdb8a7d13536c061"): 67318528 + 23166720 + 100598272 + 14180096,
+    ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
+     "cdb8a7d13536c061"): 67262720 + 16998144 + 100653312 + 14026496,
+    ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]",
+     "cdb8a7d13536c061"): 67321600 + 22690304 + 100585216 + 13876224,
+    ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
+     "cdb8a7d13536c061"): 67253760 + 22748160 + 100656896 + 14042880,
+    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 0, 0, 3, 0, 2]]",
+     "cdb8a7d13536c061"): 151976960 + 20041216,
+    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
+     "cdb8a7d13536c061"): 151983360 + 19752448,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "5f7181598bd2d594"): 151367168 + 23173888,
-    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "5f7181598bd2d594"): 151422464 + 23115008,
-    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "5f7181598bd2d594"): 151430400 + 23465472,
+     "cdb8a7d13536c061"): 151782400 + 19979520,
     ("ntt_tensor_inv_kernel<3, 8, 0, 3>", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 2]]",
-     "5f7181598bd2d594"): 151339264 + 23264000,
+     "cdb8a7d13536c061"): 151709952 + 20580352,
+    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
+     "cdb8a7d13536c061"): 151995136 + 19822336,
 }
 
 
