@@ -17,10 +17,6 @@
 
 namespace hx {
 
-#ifndef HX_TENSOR_L2PF
-#define HX_TENSOR_L2PF 1
-#endif
-
 // The tile of r_k, two elements per step (16-byte loads; row passes cover
 // whole rows, so the tile is contiguous from b_base << K), into shared memory
 // for the rounds.  Wd: the limb's word class (tensor_r3).
@@ -138,22 +134,6 @@ __global__ void __maxnreg__(NPF == 3 ? HX_TENSOR3_MAXNREG : (LOG_R == 4 ? 72 : 6
     const TensorK tk{lc.q, t.s[li], t.sp[li], lc.barrett_k, lc.barrett_qm1, t.in_mf};
     const uint64_t base = row + (c.b_base << K);
     const uint32_t TEP = padded(TE);
-    if (HX_TENSOR_L2PF && threadIdx.x == 0) {
-        // the bulk-copy unit pulls the block's operand tiles into L2 at once
-        // (contiguous, 16-byte aligned, 8 TE bytes each), so the staging
-        // steps after the first find them there instead of in DRAM
-        const uint32_t bytes = 8u * TE;
-#pragma unroll
-        for (int o = 0; o < 7; ++o) {
-            // operands A0, A1, B0, B1 then addends e0, e1, e2
-            const bool need = NPF == 3 || (o == 0 && k != 2) || (o == 1 && k != 0) ||
-                              (o == 2 && k != 2) || (o == 3 && k != 0) || o == 4 + (int)k;
-            const uint64_t* src = (o < 4 ? t.A + o * S : t.E + (o - 4) * S) + base;
-            if (need)
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes)
-                             : "memory");
-        }
-    }
     if (lc.narrow) {
         tensor_tile_to_smem<0, LOG_R, K, NPF>(sm, t, tk, base, S, k, c.nthreads, TEP);
         if constexpr (TWS) cp_async_wait<0>();
