@@ -128,23 +128,23 @@ def kernel_source_hash():
 #: capture commands.
 TRAFFIC_BYTES = {
     ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]",
-     "cdb8a7d13536c061"): 67318528 + 23166720 + 100598272 + 14180096,
+     "1d4e067c5cdc441c"): 67322112 + 22412800 + 100584448 + 14029312,
     ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
-     "cdb8a7d13536c061"): 67262720 + 16998144 + 100653312 + 14026496,
+     "1d4e067c5cdc441c"): 67253504 + 16961024 + 100664576 + 13915904,
     ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]",
-     "cdb8a7d13536c061"): 67321600 + 22690304 + 100585216 + 13876224,
+     "1d4e067c5cdc441c"): 67326720 + 22699008 + 100584192 + 13888000,
     ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
-     "cdb8a7d13536c061"): 67253760 + 22748160 + 100656896 + 14042880,
+     "1d4e067c5cdc441c"): 67254528 + 23042560 + 100659200 + 14094080,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "cdb8a7d13536c061"): 151976960 + 20041216,
+     "1d4e067c5cdc441c"): 151010304 + 20436736,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "cdb8a7d13536c061"): 151983360 + 19752448,
+     "1d4e067c5cdc441c"): 151013632 + 20715776,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "cdb8a7d13536c061"): 151782400 + 19979520,
+     "1d4e067c5cdc441c"): 151012608 + 20465664,
     ("ntt_tensor_inv_kernel<3, 8, 0, 3>", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 2]]",
-     "cdb8a7d13536c061"): 151709952 + 20580352,
+     "1d4e067c5cdc441c"): 150952960 + 22492416,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "cdb8a7d13536c061"): 151995136 + 19822336,
+     "1d4e067c5cdc441c"): 151008000 + 20422144,
 }
 
 
