@@ -179,9 +179,10 @@ def _kernel_shape(kid, N):
 def kernel_slots(kid, N, moduli, n_ct=1, per_butterfly=None):
     """Algorithmic IMAD work of one launch of a timed kernel in the step: a
     pass over its K stages (four polynomials forward, three inverse), a
-    cluster-fused launch over all stages, or a fused pass (the element-wise
+    cluster-fused launch over all stages, a fused pass (the element-wise
     tensor step plus its inverse stages on three polynomials per ciphertext
-    pair).  An inverse launch that ends the transform also scales by N^-1
+    pair), or the step kernel (the same plus the forward's K row stages on
+    the four operands).  An inverse launch that ends the transform also scales by N^-1
     (Algorithm GS's final loop): folded into its last stage, that is one
     more Shoup product per butterfly there.  In IMAD slots by default; with
     per_butterfly=ops_per_butterfly, the plain operation count (butterflies
@@ -193,6 +194,10 @@ def kernel_slots(kid, N, moduli, n_ct=1, per_butterfly=None):
         bfly += sum(N // 2 * per(q) for q in moduli)
     if tensor:
         extra = 0 if per_butterfly else sum(N * slots_per_tensor_position(q) for q in moduli)
+        if (kid >> 16) & 1:
+            # the step kernel: the forward's row stages on four polynomials
+            # as well, as many stages as the inverse's
+            return n_ct * (7 * bfly + extra)
         return n_ct * (3 * bfly + extra)
     return (4 if fwd else 3) * n_ct * bfly
 
@@ -200,8 +205,9 @@ def kernel_slots(kid, N, moduli, n_ct=1, per_butterfly=None):
 def kernel_bytes(kid, N, n_limbs, n_ct=1):
     """Algorithmic HBM bytes of one launch: a pass or a transform reads and
     writes each coefficient once (four polynomials forward, three inverse);
-    the tensor-fused launch reads the seven operands (A0, A1, B0, B1, e0, e1,
-    e2) and writes its three outputs."""
+    the tensor-fused launch and the step kernel read the seven operands
+    (A0, A1, B0, B1 -- spectra, or the forward's column pass output -- and
+    e0, e1, e2) and write their three outputs."""
     kind, fwd, K, ends_inv, tensor = _kernel_shape(kid, N)
     if tensor:
         return 10 * 8 * N * n_limbs * n_ct

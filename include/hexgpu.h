@@ -291,6 +291,30 @@ int hx_tensor_fma_inverse(hx_plan_t plan, uint64_t* d_out0, uint64_t* d_out1, ui
                           const uint64_t* d_e1, const uint64_t* d_e2, uint32_t n_polys,
                           uint32_t input_mod_factor, hx_stream_t stream);
 
+/* hx_ciphertext_step: the whole ciphertext tensor product (the computation of
+ *   hx_ciphertext_tensor) on operands laid out back to back, with the
+ *   operands kept: d_in holds a0 | a1 | b0 | b1 ([4][n_ct][limbs][N], in
+ *   [0, q)), d_e the addends e0 | e1 | e2 ([3][n_ct][limbs][N], in [0, q), NTT
+ *   domain), h_scalars one s_l in [0, q) per limb (host); d_result receives
+ *   out0 | out1 | out2 ([3][n_ct][limbs][N], in [0, q)):
+ *     out_k = InvNTT(d_k s_l + e_k),  d0 = A0 B0, d1 = A0 B1 + A1 B0,
+ *     d2 = A1 B1,  A_i, B_i = NTT(a_i, b_i)           (Section 2.2, Listing 4)
+ *   d_work ([4][n_ct][limbs][N]) is scratch the caller provides; it may equal
+ *   d_in (the operands are then overwritten).  When the plan's forward and
+ *   inverse schedules are both two-pass with the same row tiles (8 elements a
+ *   thread, 6..9 row stages), the call is three launches: the forward's column
+ *   pass, one kernel that runs the forward's row stages on the four operands,
+ *   the tensor step and the inverse's row stages on the three outputs with
+ *   the spectra kept in shared memory (they never reach HBM), and the
+ *   inverse's column pass; otherwise hx_ntt_forward into d_work followed by
+ *   hx_tensor_fma_inverse.  Both give the same bits.  Moduli must be < 2^61;
+ *   d_result must not overlap d_in, d_work or d_e.  Pointers 16-byte aligned.
+ *   Errors: HX_ERR_NULL, HX_ERR_ARG, HX_ERR_MODULUS, HX_ERR_ALIGN,
+ *   HX_ERR_OVERLAP, HX_ERR_CUDA. */
+int hx_ciphertext_step(hx_plan_t plan, uint64_t* d_result, const uint64_t* d_in,
+                       uint64_t* d_work, const uint64_t* h_scalars, const uint64_t* d_e,
+                       uint32_t n_ct, hx_stream_t stream);
+
 /* Fused element-wise part of hx_ciphertext_tensor on its own: reads A0, A1,
  * B0, B1 in [0, input_mod_factor q) (input_mod_factor in {1, 2, 4}) and e_k
  * in [0, q), writes r_k in [0, q).  Rows of n elements, [n_polys][n_limbs][n]. */

@@ -23,6 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["plan.cpp", "capi.cpp", "ntt.cu", "ntt_f1.cu", "ntt_f2.cu", "ntt_i1.cu", "ntt_i2.cu",
            "ntt_f1s.cu", "ntt_f2s.cu", "ntt_i1s.cu", "ntt_i2s.cu", "ntt_tensor.cu", "ntt_tensor3.cu",
            "ntt_cluster_f.cu", "ntt_cluster_i.cu", "ntt_cluster_t.cu", "ntt_mul.cu", "ntt_muls.cu",
+           "ntt_ctrow.cu",
            "eltwise.cu", "probe.cu",
            "batch.cu"]
 

@@ -45,6 +45,7 @@ _SIGS = {
     "hx_dyadic_inverse": [VP, VP, VP, VP, U32, U32, VP],
     "hx_ciphertext_tensor": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, VP],
     "hx_tensor_fma_inverse": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, U32, VP],
+    "hx_ciphertext_step": [VP, VP, VP, VP, P64, VP, U32, VP],
     "hx_dyadic_tensor_fma": [VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U64, P64, U32, U32,
                              U32, VP],
     "hx_ragged_set_split": [U32, U32],
@@ -457,6 +458,15 @@ def hx_tensor_fma_inverse(plan, out0, out1, out2, A0, A1, B0, B1, scalars, e0, e
     _check("hx_tensor_fma_inverse", load().hx_tensor_fma_inverse(
         _h(plan), ptr(out0), ptr(out1), ptr(out2), ptr(A0), ptr(A1), ptr(B0), ptr(B1),
         host_u64(scalars), ptr(e0), ptr(e1), ptr(e2), n_polys, input_mod_factor,
+        _stream(stream)))
+
+
+def hx_ciphertext_step(plan, result, inputs, work, scalars, e, n_ct: int, stream=None):
+    """result = out0 | out1 | out2 of the ciphertext tensor product of
+    inputs = a0 | a1 | b0 | b1 (back to back), addends e = e0 | e1 | e2;
+    work is the caller's [4][n_ct][limbs][N] scratch (may be inputs)."""
+    _check("hx_ciphertext_step", load().hx_ciphertext_step(
+        _h(plan), ptr(result), ptr(inputs), ptr(work), host_u64(scalars), ptr(e), n_ct,
         _stream(stream)))
 
 

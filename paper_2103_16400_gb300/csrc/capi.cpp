@@ -325,6 +325,35 @@ int hx_tensor_fma_inverse(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* 
     return HX_OK;
 }
 
+int hx_ciphertext_step(hx_plan_t plan, uint64_t* r, const uint64_t* in, uint64_t* work,
+                       const uint64_t* h_scalars, const uint64_t* e, uint32_t n_ct,
+                       hx_stream_t stream) {
+    if (!plan || !r || !in || !work || !h_scalars || !e) return HX_ERR_NULL;
+    if (n_ct == 0 || (uint64_t)n_ct * 4 * plan->n_limbs > (1ull << 31)) return HX_ERR_ARG;
+    for (uint32_t l = 0; l < plan->n_limbs; ++l) {
+        const uint64_t q = plan->moduli[l];
+        if (q >= (1ull << 61)) return HX_ERR_MODULUS;
+        if (h_scalars[l] >= q) return HX_ERR_ARG;
+    }
+    if (!aligned16(r) || !aligned16(in) || !aligned16(work) || !aligned16(e)) return HX_ERR_ALIGN;
+    const uint64_t S = (uint64_t)n_ct * plan->n_limbs * plan->N;
+    const uintptr_t x = (uintptr_t)r, xe = x + 3 * S * 8;
+    const uintptr_t a = (uintptr_t)in, ae = a + 4 * S * 8;
+    const uintptr_t w = (uintptr_t)work, we = w + 4 * S * 8;
+    const uintptr_t ea = (uintptr_t)e, ee = ea + 3 * S * 8;
+    if ((x < ae && a < xe) || (x < we && w < xe) || (x < ee && ea < xe) ||
+        (w < ee && ea < we) || (w != a && w < ae && a < we))
+        return HX_ERR_OVERLAP;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (ct_step_fusable(plan->cfg_fwd, plan->cfg_inv))
+        return cuda_status(
+            launch_ct_step(plan, r, in, work, e, n_ct, h_scalars, plan->cfg_fwd, plan->cfg_inv, s));
+    int st = hx_ntt_forward(plan, work, in, 4 * n_ct, 1, 4, stream);
+    if (st != HX_OK) return st;
+    return hx_tensor_fma_inverse(plan, r, r + S, r + 2 * S, work, work + S, work + 2 * S,
+                                 work + 3 * S, h_scalars, e, e + S, e + 2 * S, n_ct, 4, stream);
+}
+
 int hx_ciphertext_tensor(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* o2, uint64_t* a0,
                          uint64_t* a1, uint64_t* b0, uint64_t* b1, const uint64_t* h_scalars,
                          const uint64_t* e0, const uint64_t* e1, const uint64_t* e2,

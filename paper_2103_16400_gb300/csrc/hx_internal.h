@@ -87,7 +87,8 @@ void count_launch(uint64_t n = 1);
 // (K1 for kind 3), 12-13 polynomials (outputs for the fused pass; for kind 3
 // bit 12 marks the tensor-fused inverse) per block, 14 staged twiddles,
 // 15-19 K2 (kind 3); for kind 0, bit 15 marks the inverse's first pass with
-// the dyadic product fused in.
+// the dyadic product fused in; for kind 2, bit 16 marks the step kernel that
+// also runs the forward's row stages (ntt_ctrow.cu).
 uint32_t timing_begin(cudaStream_t s, uint32_t kernel);
 void timing_end(uint32_t slot, cudaStream_t s);
 
@@ -123,6 +124,17 @@ cudaError_t launch_mul_inverse(const hx_plan_s* plan, uint64_t* out, const uint6
 cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const uint64_t* A,
                                   const uint64_t* E, uint32_t n_ct, const uint64_t* h_scalars,
                                   uint32_t in_mf, const NttCfg& cfg, cudaStream_t stream);
+// The whole ciphertext step in three launches: the forward's column pass
+// (in -> work, the four operands back to back), the forward's row stages,
+// the tensor and the inverse's row stages in one kernel (work, E -> out,
+// ntt_ctrow.cu), the inverse's column pass (out, in place).  Needs both
+// schedules two-pass with the same row tiles (ct_step_fusable), else
+// cudaErrorNotSupported.
+bool ct_step_fusable(const NttCfg& f, const NttCfg& i);
+cudaError_t launch_ct_step(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
+                           uint64_t* work, const uint64_t* E, uint32_t n_ct,
+                           const uint64_t* h_scalars, const NttCfg& f, const NttCfg& i,
+                           cudaStream_t stream);
 
 // eltwise.cu
 enum EltOp { ELT_ADD = 0, ELT_SUB = 1, ELT_MULT = 2, ELT_FMA = 3, ELT_NEG = 4 };

@@ -478,4 +478,77 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
     return cudaSuccess;
 }
 
+
+// The step's two row passes fused around the tensor (ntt_ctrow.cu): both
+// schedules two-pass, their row passes over the same stages in the same row
+// tiles with 8 elements a thread.
+bool ct_step_fusable(const NttCfg& f, const NttCfg& i) {
+    if (f.npass != 2 || i.npass != 2 || is_cluster(f) || is_cluster(i)) return false;
+    const PassCfg& fr = f.pass[1];
+    const PassCfg& ir = i.pass[1];
+    if (fr.logGc != 0 || ir.logGc != 0 || fr.s0 != ir.s0 || fr.K != ir.K ||
+        fr.logGb != ir.logGb || fr.logR != 3 || ir.logR != 3)
+        return false;
+    if (!pick_ct_row(3, fr.K)) return false;
+    return (size_t)8 * 4 * padded(1u << (fr.logGb + fr.K)) <= 192 * 1024;
+}
+
+cudaError_t launch_ct_step(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
+                           uint64_t* work, const uint64_t* E, uint32_t n_ct,
+                           const uint64_t* h_scalars, const NttCfg& f, const NttCfg& i,
+                           cudaStream_t stream) {
+    if (!ct_step_fusable(f, i)) return cudaErrorNotSupported;
+    const int L = plan->logN;
+    // the forward's column pass over the four operands
+    cudaError_t e = launch_pass(plan, f.pass[0], work, in, 4 * n_ct, true, false, 4, stream);
+    if (e != cudaSuccess) return e;
+    const PassCfg& p = f.pass[1];
+    TensorPassKernel k = pick_ct_row(3, p.K);
+    PassArgs a{};
+    a.out = out;
+    a.in = nullptr;
+    a.limbs = plan->d_limbs;
+    a.order = plan->d_order;   // few long blocks: the costliest limbs start first
+    a.n_limbs = plan->n_limbs;
+    a.n_polys = 3 * n_ct;
+    a.L = L;
+    a.s0 = p.s0;
+    a.logGb = p.logGb;
+    a.logGc = 0;
+    a.log_tiles_c = 0;
+    a.last = 0;
+    a.out_mf = 1;
+    const int logTE = p.logGb + p.K;
+    const uint32_t tiles = 1u << (L - logTE);
+    const uint32_t threads = 1u << (logTE - 3);
+    const size_t smem = (size_t)8 * 4 * padded(1u << logTE);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    for (uint32_t limb0 = 0; limb0 < plan->n_limbs; limb0 += kTensorLimbs) {
+        const uint32_t chunk = std::min<uint32_t>(kTensorLimbs, plan->n_limbs - limb0);
+        TensorIn t{};
+        t.A = work;
+        t.E = E;
+        t.n_ct = n_ct;
+        t.in_mf = 4;
+        t.limb0 = limb0;
+        for (uint32_t l = 0; l < chunk; ++l) {
+            const uint64_t q = plan->moduli[limb0 + l], sc = h_scalars[limb0 + l];
+            t.s[l] = sc;
+            t.sp[l] = (uint64_t)(((unsigned __int128)sc << 64) / q);
+        }
+        const uint32_t slot =
+            timing_begin(stream, 2u | (3u << 4) | ((uint32_t)p.K << 7) | (1u << 16));
+        k<<<dim3(tiles * n_ct, chunk), threads, smem, stream>>>(a, t);
+        timing_end(slot, stream);
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // the inverse's column pass over the three outputs, N^-1 folded
+    return launch_pass(plan, i.pass[0], out, out, 3 * n_ct, false, true, 1, stream);
+}
 }  // namespace hx

@@ -27,4 +27,10 @@ typedef void (*TensorPassKernel)(PassArgs, TensorIn);
 // the menu
 TensorPassKernel pick_tensor_inv(int logR, int K, bool tws, int npf);
 
+// ntt_ctrow.cu: the tensor step with both row passes around it (the
+// forward's row stages on the four operands, the tensor, the inverse's row
+// stages on the three outputs), for (elements per thread, stages); nullptr if
+// not in the menu (8 elements a thread, 6..9 stages)
+TensorPassKernel pick_ct_row(int logR, int K);
+
 }  // namespace hx

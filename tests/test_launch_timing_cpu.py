@@ -19,6 +19,7 @@ def test_kernel_names():
     assert capi.hx_kernel_name(kid(0, 0, 1, 4, 7, 1, 1)) == "ntt_pass_kernel<0, 1, 4, 7, 1, 1>"
     assert capi.hx_kernel_name(kid(1, 1, 0, 3, 9)) == "ntt_pipe_kernel<1, 0, 3, 9>"
     assert capi.hx_kernel_name(kid(2, 0, 0, 3, 9, 3)) == "ntt_tensor_inv_kernel<3, 9, 0, 3>"
+    assert capi.hx_kernel_name(kid(2, 0, 0, 3, 9, 0) | 1 << 16) == "ntt_ct_row_kernel<3, 9>"
     # cluster-fused transforms: kind 3, K1 in the K field, K2 in bits 15-19
     assert capi.hx_kernel_name(kid(3, 1, 0, 4, 8, 0) | 8 << 15) == "ntt_cluster_kernel<1, 4, 8, 8>"
     assert (capi.hx_kernel_name(kid(3, 0, 0, 4, 7, 1) | 9 << 15)
@@ -139,3 +140,18 @@ def test_step_work():
     assert nbytes == 18 * 8 * N * 32
     tensor = N * (21 * 106 + 11 * 26)
     assert slots == (4 * 16 + 3 * 17) * 32768 * (21 * 17 + 11 * 4) + tensor
+
+
+def test_step_kernel_work_is_both_row_passes_and_the_tensor():
+    """The step kernel (forward row stages on four operands, the tensor, the
+    inverse row stages on three outputs): its slots are the forward row
+    pass's plus the fused pass's, its bytes the fused pass's (seven operands
+    in, three out)."""
+    N, moduli = 1 << 16, W.mixed_width_primes(32)
+    step = kid(2, 0, 0, 3, 9, 0) | 1 << 16
+    fused = bench.kernel_slots(kid(2, 0, 0, 3, 9, 3), N, moduli)
+    fwd_row = bench.kernel_slots(kid(0, 1, 0, 3, 9), N, moduli)
+    assert bench.kernel_slots(step, N, moduli) == fused + fwd_row
+    ops = bench.kernel_slots(step, N, moduli, per_butterfly=bench.ops_per_butterfly)
+    assert ops == 7 * 9 * (N // 2) * (21 * 10 + 11 * 3)
+    assert bench.kernel_bytes(step, N, 32) == bench.kernel_bytes(kid(2, 0, 0, 3, 9, 3), N, 32)
