@@ -259,22 +259,33 @@ STEP_STREAMS = 2
 
 
 class HexStep:
-    """The timed step, through the C ABI, with autotuned schedules: one
-    forward call over the four inputs, the fused tensor/FMA kernel, one
-    inverse call over the three outputs.  Step i runs on stream i mod
-    `n_streams` with that stream's own preallocated buffers (A: the four
-    spectra, R: the three results), so steps on different streams overlap
-    and every step does its whole work on its own batch."""
+    """The timed step, through the C ABI, with autotuned schedules: the
+    ciphertext product of four inputs into three results.  It runs as
+    hx_ciphertext_step (three launches: the forward's column pass, one kernel
+    for the forward's row stages, the tensor step and the inverse's row
+    stages, the inverse's column pass) on a plan tuned for that call, unless
+    the composition -- one forward call over the four inputs, then the
+    tensor/FMA step fused into the inverse of the three outputs, on a plan
+    tuned for those two calls -- times faster.  Step i runs on stream
+    i mod `n_streams` with that stream's own preallocated buffers (A: the
+    four spectra or the forward column pass's output, R: the three results),
+    so steps on different streams overlap and every step does its whole work
+    on its own batch."""
 
-    def __init__(self, N, moduli, s, dev_sets, torch, tune=True, n_streams=STEP_STREAMS):
+    def __init__(self, N, moduli, s, dev_sets, torch, tune=True, n_streams=STEP_STREAMS,
+                 path=None):
         from paper_2103_16400_gb300 import capi, tune as hx_tune
         from paper_2103_16400_gb300.tensors import empty
         self.capi, self.torch = capi, torch
         self.N, self.moduli, self.s = N, moduli, s
-        self.plan = capi.Plan(N, moduli)
+        self.plan = capi.Plan(N, moduli)          # the composition's two calls
+        self.step_plan = capi.Plan(N, moduli)     # hx_ciphertext_step (tables shared)
+        self.tuned = {}
         if tune:
             self.tuned = {"forward": hx_tune.tune(self.plan, 4, direction=capi.Plan.FORWARD),
-                          "inverse": hx_tune.tune_tensor(self.plan, 1, s)}
+                          "inverse": hx_tune.tune_tensor(self.plan, 1, s),
+                          "step": hx_tune.tune_step(self.step_plan, 1, s, iters=8,
+                                                    streams=n_streams)}
         self.dev_sets = dev_sets
         L = len(moduli)
         self.stream = torch.cuda.current_stream()
@@ -283,6 +294,29 @@ class HexStep:
         self.A, self.R = self.bufs[0]
         self.fwd_events = []
         self.inv_events = []
+        self.step_events = []
+        if path is None:
+            times = {p: self.time_path(p) for p in ("step", "composed")}
+            path = min(times, key=times.get)
+            self.path_us = times
+        self.path = path
+
+    def time_path(self, path, n=100):
+        """Mean device time of one step by one path, the steps alternating
+        over the step streams as the timed region runs them."""
+        torch = self.torch
+        for i in range(4):
+            self.run(i, path=path)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        self.begin(e0)
+        for i in range(n):
+            self.run(i, path=path)
+        self.join()
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / n
 
     def begin(self, ev):
         """Every step stream waits for `ev` (recorded on the first stream)."""
@@ -296,23 +330,36 @@ class HexStep:
             e.record(st)
             self.stream.wait_event(e)
 
-    def run(self, i, record=False, one_stream=False):
+    def run(self, i, record=False, one_stream=False, path=None):
         """Step i: on stream i mod n_streams (on the first stream alone with
-        one_stream, or when recording per-call events)."""
+        one_stream, or when recording per-call events), by `path` ("step" or
+        "composed"; the chosen one by default).  With record, the composed
+        path records its two calls' events, the step path its call's."""
         c, N = self.capi, self.N
+        path = path or self.path
         k = 0 if (one_stream or record) else i % len(self.streams)
         st = self.streams[k]
         self.A, self.R = self.bufs[k]
         ins, es = self.dev_sets[i % len(self.dev_sets)]
+        A, R = self.A, self.R
+        if path == "step":
+            if record:
+                e0 = self.torch.cuda.Event(enable_timing=True)
+                e1 = self.torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+            c.hx_ciphertext_step(self.step_plan, R, ins, A, self.s, es, 1, st)
+            if record:
+                e1.record(st)
+                self.step_events.append((e0, e1))
+            return [R[0:1], R[1:2], R[2:3]]
         if record:
             e0 = self.torch.cuda.Event(enable_timing=True)
             e1 = self.torch.cuda.Event(enable_timing=True)
             e0.record(st)
-        c.hx_ntt_forward(self.plan, self.A, ins, 4, 1, 4, st)
+        c.hx_ntt_forward(self.plan, A, ins, 4, 1, 4, st)
         if record:
             e1.record(st)
             self.fwd_events.append((e0, e1))
-        A, R = self.A, self.R
         # tensor, FMA and inverse NTT: the element-wise step runs inside the
         # inverse's first pass (operands back to back)
         c.hx_tensor_fma_inverse(self.plan, R[0], R[1], R[2], A[0], A[1], A[2], A[3], self.s,
@@ -322,6 +369,10 @@ class HexStep:
             e2.record(st)
             self.inv_events.append((e1, e2))
         return [R[0:1], R[1:2], R[2:3]]
+
+    def kernel_plan(self):
+        """The plan whose schedules the timed step's kernels run."""
+        return self.step_plan if self.path == "step" else self.plan
 
 
 # ------------------------------------------------------------------ ragged batch
@@ -1102,11 +1153,15 @@ def main():
     calls_steps = min(args.steps, 200)
     step.fwd_events.clear()
     step.inv_events.clear()
+    step.step_events.clear()
     for i in range(calls_steps):
-        step.run(i, record=True)
+        step.run(i, record=True, path="composed")
+        if step.path == "step":
+            step.run(i, record=True, path="step")
     torch.cuda.synchronize()
     fwd_ms = [a.elapsed_time(b) for a, b in step.fwd_events]
     inv_ms = [a.elapsed_time(b) for a, b in step.inv_events]
+    step_call_ms = [a.elapsed_time(b) for a, b in step.step_events]
 
     # kernel-timing region: the same steps again with the library's events
     # around every launch (each pair adds a start-up bubble of a microsecond
@@ -1190,8 +1245,9 @@ def main():
         dom = kernels[dom_id]
         r = op_roofline(dom["alg_ops_per_launch"], dom["alg_bytes_per_launch"], dom["avg_us"],
                         imad_rate, hbm_gbs)
-        dom_traffic = traffic_for(dom["kernel"], inv_sched if not (dom_id >> 2) & 1
-                                  else fwd_sched) if (N, nl) == (1 << 16, 32) else None
+        kp = step.kernel_plan()
+        dom_traffic = traffic_for(dom["kernel"], kp.schedule(kp.INVERSE) if not (dom_id >> 2) & 1
+                                  else kp.schedule(kp.FORWARD)) if (N, nl) == (1 << 16, 32) else None
         roofline = dict(
             r, traffic=dom_traffic,
             traffic_unit="DRAM bytes per launch (ncu, this build's sources), else null",
@@ -1214,7 +1270,12 @@ def main():
                           "frac_slots": roofline_forward_call["slots"]["frac"],
                           "us": fwd_call_ms * 1e3},
             step=step_roof,
-            schedules=roofline_forward_call["schedules"])
+            schedules=dict(roofline_forward_call["schedules"],
+                           step={"forward": [list(p) for p in
+                                             step.step_plan.schedule(step.step_plan.FORWARD)],
+                                 "inverse": [list(p) for p in
+                                             step.step_plan.schedule(step.step_plan.INVERSE)]},
+                           path=step.path))
 
     # the plain forward and inverse calls on their own: the goal's forward +
     # inverse figure, carried inside the roofline object as well
@@ -1240,7 +1301,7 @@ def main():
     host_out = [torch.empty((3, 1, nl, N), dtype=torch.int64).pin_memory() for _ in range(2)]
     h2d = sum(x.numel() * 8 for x in host_in[0])
     d2h = host_out[0].numel() * 8
-    pipe = TensorPipeline(step.plan, s, 1, depth=2)
+    pipe = TensorPipeline(step.kernel_plan(), s, 1, depth=2)
     for i in range(3):
         pipe.submit(*host_in[i % len(host_in)], host_out[i % 2])
     pipe.synchronize()
@@ -1282,8 +1343,15 @@ def main():
                       "tensor_inverse_us": float(np.mean(inv_ms)) * 1e3,
                       "tensor_inverse_limb_transforms_per_s":
                           3 * nl / (float(np.mean(inv_ms)) * 1e-3),
+                      "step_path": step.path,
+                      "step_us": (float(np.mean(step_call_ms)) * 1e3 if step_call_ms
+                                  else (fwd_call_ms + inv_call_ms) * 1e3),
+                      "path_us": getattr(step, "path_us", None),
                       "how": f"CUDA events around each call, {calls_steps} steps in a "
-                             f"region after the timed one"},
+                             f"region after the timed one; step_us: the step's own call(s) "
+                             f"(hx_ciphertext_step on the path 'step', the forward call plus "
+                             f"the tensor + inverse call on 'composed'); path_us: both paths "
+                             f"timed as the timed region runs them, the faster one taken"},
             "gpu_launches": launches,
             "clocks": clocks.summary()}
     # the secondary reports run on rank 0 only; the other ranks wait.  A

@@ -2,9 +2,10 @@
 
 One batch is the ciphertext product of hx_ciphertext_tensor on operands that
 live in pinned host memory: upload the four input polynomials (a0, a1, b0,
-b1) and the three addends (e0, e1, e2), run the forward NTT of the four and
-hx_tensor_fma_inverse (tensor, FMA and inverse NTT, the element-wise step
-fused into the inverse's first pass), download the three results.
+b1) and the three addends (e0, e1, e2), run hx_ciphertext_step on them in
+place (forward NTT, tensor, FMA and inverse NTT: three launches when the
+plan's schedules share their row passes, else the forward call and the
+fused inverse), download the three results.
 
 The host link is slower than the transforms (about 0.2 TB/s each way against
 several TB/s of HBM), so batches overlap: three CUDA streams -- upload,
@@ -73,10 +74,9 @@ class TensorPipeline:
         s.wait_event(self.up_done[k])
         if self.used[k]:
             s.wait_event(self.down_done[k])
-        nc = self.n_ct
-        capi.hx_ntt_forward(self.plan, A, A, 4 * nc, 1, 4, s)
-        capi.hx_tensor_fma_inverse(self.plan, R[0], R[1], R[2], A[0], A[1], A[2], A[3],
-                                   self.scalars, E[0], E[1], E[2], nc, 4, s)
+        # the whole product in place on A: three launches when the plan's
+        # schedules allow (hx_ciphertext_step), else forward + fused inverse
+        capi.hx_ciphertext_step(self.plan, R, A, A, self.scalars, E, self.n_ct, s)
         self.comp_done[k].record(s)
         with torch.cuda.stream(self.s_down):
             self.s_down.wait_event(self.comp_done[k])

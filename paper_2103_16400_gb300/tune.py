@@ -365,6 +365,114 @@ def tune_tensor(plan: "capi.Plan", n_ct: int, scalars, iters: int = 5, use_cache
     return out
 
 
+# ---------------------------------------------------------------- the ciphertext step
+def step_candidates(logN: int) -> List[Tuple[List[Pass], List[Pass]]]:
+    """(forward, inverse) schedule pairs under which hx_ciphertext_step runs
+    as three launches: both two-pass, the row passes over the same stages
+    K1 .. logN-1 (6..9 of them) in the same 2^logGb-row tiles with 8
+    elements a thread (32..512 threads, four padded tiles within 192 KB of
+    shared memory); the column passes' tile widths and the inverse column
+    pass's twiddle staging vary."""
+    out = []
+    for K1 in splits(logN):
+        K2 = logN - K1
+        if not 6 <= K2 <= 9:
+            continue
+        for logGb in range(0, 4):
+            te = 1 << (logGb + K2)
+            if not 5 <= logGb + K2 - 3 <= 9 or 8 * 4 * (te + te // 16) > 192 * 1024:
+                continue
+            for fc in (3, 4):
+                for ic in (3, 4):
+                    for ipipe in (0, 2):
+                        out.append(([(0, K1, 0, fc, 4, 0, 1), (K1, K2, logGb, 0, 3, 0, 1)],
+                                    [(0, K1, 0, ic, 4, ipipe, 1), (K1, K2, logGb, 0, 3, 0, 2)]))
+    return out
+
+
+def tune_step(plan: "capi.Plan", n_ct: int, scalars, iters: int = 5, use_cache: bool = True,
+              verbose: bool = False, streams: int = 1) -> Optional[dict]:
+    """Pick the (forward, inverse) schedule pair for hx_ciphertext_step on
+    n_ct ciphertext pairs by timing the call itself over step_candidates
+    (the three best re-timed four times as long), apply it to the plan and
+    return {"forward", "inverse", "us", "tried"}; None when log2 N has no
+    candidate (the call then runs as the composition).  With streams > 1
+    consecutive calls alternate over that many CUDA streams, each with its
+    own output and scratch buffers (independent products overlapping, a
+    throughput setting).  Cached like tune()."""
+    import torch
+    from .tensors import to_device, empty
+    import numpy as np
+
+    cands = [c for c in step_candidates(plan.N.bit_length() - 1)
+             if valid(plan, c[0]) and valid(plan, c[1])]
+    if not cands:
+        return None
+    name = torch.cuda.get_device_name()
+    key = _key(plan.N, plan.moduli, n_ct, name) + f"|ciphertext_step|S={streams}"
+    if use_cache:
+        with _lock:
+            hit = load_cache().get(key)
+        if hit:
+            f = [tuple(p) for p in hit["forward"]]
+            i = [tuple(p) for p in hit["inverse"]]
+            if valid(plan, f) and valid(plan, i):
+                plan.set_schedule(f, plan.FORWARD)
+                plan.set_schedule(i, plan.INVERSE)
+                return dict(hit, cached=True)
+    rng = np.random.default_rng(3)
+    shape = (n_ct, plan.n_limbs, plan.N)
+
+    def operand(k):
+        h = np.empty((k,) + shape, dtype=np.uint64)
+        for l, q in enumerate(plan.moduli):
+            h[:, :, l] = rng.integers(0, q, size=(k, n_ct, plan.N), dtype=np.uint64)
+        return to_device(h)
+
+    X, E = operand(4), operand(3)
+    st = torch.cuda.current_stream()
+    sts = [st] + [torch.cuda.Stream() for _ in range(streams - 1)]
+    bufs = [(empty((4,) + shape), empty((3,) + shape)) for _ in sts]
+
+    def timer(pair, n):
+        plan.set_schedule(pair[0], plan.FORWARD)
+        plan.set_schedule(pair[1], plan.INVERSE)
+        for k, s in enumerate(sts):
+            capi.hx_ciphertext_step(plan, bufs[k][1], X, bufs[k][0], scalars, E, n_ct, s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for s in sts[1:]:
+            s.wait_event(e0)
+        for j in range(n):
+            k = j % len(sts)
+            capi.hx_ciphertext_step(plan, bufs[k][1], X, bufs[k][0], scalars, E, n_ct, sts[k])
+        for s in sts[1:]:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            st.wait_event(ev)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / n
+
+    first = sorted((timer(c, iters), k) for k, c in enumerate(cands))
+    final = sorted((timer(cands[k], 4 * iters), k) for _, k in first[:3])
+    us, k = final[0]
+    f, i = cands[k]
+    plan.set_schedule(f, plan.FORWARD)
+    plan.set_schedule(i, plan.INVERSE)
+    if verbose:
+        print(f"ciphertext step: {us:.1f} us, forward {f}, inverse {i}")
+    out = {"forward": [list(p) for p in f], "inverse": [list(p) for p in i], "us": us,
+           "tried": len(cands)}
+    if use_cache:
+        with _lock:
+            cache = load_cache()
+            cache[key] = out
+            save_cache(cache)
+    return out
+
+
 # ---------------------------------------------------------------- ragged batches
 def ragged_splits(log2_n: int) -> List[int]:
     """Column-pass stage counts the ragged kernels can run at N = 2^log2_n

@@ -89,3 +89,26 @@ def test_cluster_options_fit_the_menu():
         for a, b in opts:
             c = b[1] - a[3]
             assert a[5] == b[5] == 3 and 1 <= c <= 4 and a[1] - b[2] == c
+
+
+def test_step_candidates_share_their_row_passes():
+    """Every (forward, inverse) pair offered for hx_ciphertext_step: both
+    two-pass, row passes over the same stages (6..9) in the same row tiles
+    with 8 elements a thread and 32..512 threads, four padded tiles within
+    192 KB; none at N where no row pass can have 6..9 stages."""
+    for logN in (14, 15, 16, 17):
+        cands = tune.step_candidates(logN)
+        assert cands
+        for f, i in cands:
+            assert len(f) == len(i) == 2
+            assert f[0][0] == i[0][0] == 0 and f[0][1] == i[0][1]
+            fr, ir = f[1], i[1]
+            assert fr[:5] == ir[:5] and fr[3] == 0 and fr[4] == 3
+            assert fr[0] + fr[1] == logN and 6 <= fr[1] <= 9
+            assert 5 <= fr[2] + fr[1] - 3 <= 9
+            te = 1 << (fr[2] + fr[1])
+            assert 32 * (te + te // 16) <= 192 * 1024
+            assert ir[6] == 2 and fr[6] == 1
+    assert tune.step_candidates(10) == []
+    assert len({(tuple(f), tuple(i)) for f, i in tune.step_candidates(16)}) == \
+        len(tune.step_candidates(16))
