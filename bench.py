@@ -122,29 +122,36 @@ def kernel_source_hash():
 
 #: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) at N = 65536 x 32
 #: mixed limbs from ncu captures, keyed by (kernel name or "forward_call",
-#: schedule JSON, kernel_source_hash() of the captured build).  A key whose
+#: schedule JSON -- the inverse schedule for the fused tensor pass and the
+#: step kernel --, kernel_source_hash() of the captured build).  A key whose
 #: hash is not the running build's gives no figure (the field is null), so a
 #: changed kernel never reports stale traffic.  profiles/ records the
 #: capture commands.
 TRAFFIC_BYTES = {
-    ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]",
-     "1d4e067c5cdc441c"): 67322112 + 22412800 + 100584448 + 14029312,
     ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
-     "1d4e067c5cdc441c"): 67253504 + 16961024 + 100664576 + 13915904,
+     "ad1c7d1e134c893b"): 67254016 + 17140224 + 100653056 + 14171648,
+    ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]",
+     "ad1c7d1e134c893b"): 67318528 + 22884864 + 100587520 + 14384384,
     ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]",
-     "1d4e067c5cdc441c"): 67326720 + 22699008 + 100584192 + 13888000,
+     "ad1c7d1e134c893b"): 67336960 + 22652416 + 100587008 + 13977856,
     ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
-     "1d4e067c5cdc441c"): 67254528 + 23042560 + 100659200 + 14094080,
-    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "1d4e067c5cdc441c"): 151010304 + 20436736,
+     "ad1c7d1e134c893b"): 67252480 + 22662400 + 100652288 + 14222848,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "1d4e067c5cdc441c"): 151013632 + 20715776,
-    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "1d4e067c5cdc441c"): 151012608 + 20465664,
-    ("ntt_tensor_inv_kernel<3, 8, 0, 3>", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 2]]",
-     "1d4e067c5cdc441c"): 150952960 + 22492416,
+     "ad1c7d1e134c893b"): 151007744 + 20687360,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "1d4e067c5cdc441c"): 151008000 + 20422144,
+     "ad1c7d1e134c893b"): 151004928 + 20776448,
+    ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 0, 0, 3, 0, 2]]",
+     "ad1c7d1e134c893b"): 151005184 + 20725760,
+    ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
+     "ad1c7d1e134c893b"): 184721920 + 26239488,
+    ("ntt_ct_row_kernel<3, 8>", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 2]]",
+     "ad1c7d1e134c893b"): 184366592 + 26547200,
+    ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
+     "ad1c7d1e134c893b"): 184759808 + 26149376,
+    ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 1, 0, 3, 0, 2]]",
+     "ad1c7d1e134c893b"): 184722432 + 26258688,
+    ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
+     "ad1c7d1e134c893b"): 184761088 + 26358272,
 }
 
 
@@ -979,6 +986,8 @@ def run_case(args):
     P = args.polys
     if args.case == "tensor_inv":
         return run_tensor_inv(args, wl, torch)
+    if args.case == "ct_step":
+        return run_ct_step(args, wl, torch)
     n_sets = 2
     xs = [to_device(W.poly_batch(wl.seed + k, 0, P, wl.moduli, N)) for k in range(n_sets)]
     ys = [empty(x.shape) for x in xs]
@@ -1075,6 +1084,54 @@ def run_tensor_inv(args, wl, torch):
     return 0
 
 
+def run_ct_step(args, wl, torch):
+    """hx_ciphertext_step on one ciphertext pair with the (forward, inverse)
+    schedule pair given as --schedule '[forward, inverse]' (else the step
+    tuner's): the call's time, and the composition (forward call, then the
+    fused tensor + inverse call) on the same plan (diagnostic line)."""
+    from paper_2103_16400_gb300 import capi, tune as hx_tune
+    from paper_2103_16400_gb300.tensors import empty, to_device
+    N, nl = args.N, args.limbs
+    plan = capi.Plan(N, wl.moduli)
+    s = W.scalars(wl.seed, 20, wl.moduli)
+    if args.schedule:
+        f, i = ([tuple(p) for p in sch] for sch in json.loads(args.schedule))
+        plan.set_schedule(f, plan.FORWARD)
+        plan.set_schedule(i, plan.INVERSE)
+    else:
+        hx_tune.tune_step(plan, 1, s, verbose=bool(os.environ.get("HX_TUNE_VERBOSE")))
+    X = to_device(np.stack([W.poly_batch(wl.seed, k, 1, wl.moduli, N) for k in range(4)]))
+    E = to_device(np.stack([W.poly_batch(wl.seed, 10 + k, 1, wl.moduli, N) for k in range(3)]))
+    Wk, R = empty((4, 1, nl, N)), empty((3, 1, nl, N))
+    st = torch.cuda.current_stream()
+
+    def step():
+        capi.hx_ciphertext_step(plan, R, X, Wk, s, E, 1, st)
+
+    def composed():
+        capi.hx_ntt_forward(plan, Wk, X, 4, 1, 4, st)
+        capi.hx_tensor_fma_inverse(plan, R[0], R[1], R[2], Wk[0], Wk[1], Wk[2], Wk[3], s,
+                                   E[0], E[1], E[2], 1, 4, st)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / args.steps
+
+    print(json.dumps({"case": "ct_step", "N": N, "limbs": nl,
+                      "schedule": {"forward": [list(p) for p in plan.schedule(plan.FORWARD)],
+                                   "inverse": [list(p) for p in plan.schedule(plan.INVERSE)]},
+                      "step_us": timed(step), "composed_us": timed(composed)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1091,7 +1148,8 @@ def main():
                     help="skip the serving report (Poisson arrivals, p50/p99 latency)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--case", default="pipeline",
-                    choices=["pipeline", "fwd", "inv", "tensor", "tensor_inv", "probes", "serving"],
+                    choices=["pipeline", "fwd", "inv", "tensor", "tensor_inv", "ct_step", "probes",
+                             "serving"],
                     help="pipeline: the contract line; others: one kernel family alone "
                          "(diagnostic line, used for profiling)")
     ap.add_argument("--polys", type=int, default=8, help="polynomials per call for --case fwd/inv")
