@@ -201,6 +201,10 @@ def kernel_slots(kid, N, moduli, n_ct=1, per_butterfly=None):
         bfly += sum(N // 2 * per(q) for q in moduli)
     if tensor:
         extra = 0 if per_butterfly else sum(N * slots_per_tensor_position(q) for q in moduli)
+        if (kid >> 17) & 1:
+            # the product's step kernel: the forward's row stages on a and b,
+            # the inverse's on their product (the dyadic product not counted)
+            return n_ct * 3 * bfly
         if (kid >> 16) & 1:
             # the step kernel: the forward's row stages on four polynomials
             # as well, as many stages as the inverse's
@@ -216,6 +220,8 @@ def kernel_bytes(kid, N, n_limbs, n_ct=1):
     (A0, A1, B0, B1 -- spectra, or the forward's column pass output -- and
     e0, e1, e2) and write their three outputs."""
     kind, fwd, K, ends_inv, tensor = _kernel_shape(kid, N)
+    if tensor and (kid >> 17) & 1:
+        return 3 * 8 * N * n_limbs * n_ct        # the product's: a, b in, a b out
     if tensor:
         return 10 * 8 * N * n_limbs * n_ct
     return 2 * (4 if fwd else 3) * 8 * N * n_limbs * n_ct

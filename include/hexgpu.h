@@ -291,6 +291,23 @@ int hx_tensor_fma_inverse(hx_plan_t plan, uint64_t* d_out0, uint64_t* d_out1, ui
                           const uint64_t* d_e1, const uint64_t* d_e2, uint32_t n_polys,
                           uint32_t input_mod_factor, hx_stream_t stream);
 
+/* hx_poly_product: d_result = d_a * d_b in R_q = Z_q[X]/(X^N + 1) (the paper's
+ *   Listing 4: forward NTT of both, EltwiseMultMod with input_mod_factor 4,
+ *   inverse NTT to [0, q)) with the operands kept: d_a, d_b in [0, q), only
+ *   read; d_work ([2][n_polys][limbs][N]) is scratch the caller provides,
+ *   apart from d_a, d_b and d_result; d_result may equal d_a or d_b.  When
+ *   the plan's forward and inverse schedules are both two-pass over the same
+ *   stages with 8 elements a thread in their row passes, the call is four
+ *   launches: the forward's column pass of a and of b, one kernel that runs
+ *   the forward's row stages on both, the dyadic product and the inverse's
+ *   row stages (in the inverse's row tiles) with the spectra in shared
+ *   memory, and the inverse's column pass; otherwise hx_ntt_forward of each
+ *   into d_work followed by hx_dyadic_inverse.  Both give the same bits.
+ *   Moduli below 2^62.  All [n_polys][plan n_limbs][N], 16-byte aligned.
+ *   Errors: HX_ERR_NULL, HX_ERR_ARG, HX_ERR_ALIGN, HX_ERR_OVERLAP, HX_ERR_CUDA. */
+int hx_poly_product(hx_plan_t plan, uint64_t* d_result, const uint64_t* d_a, const uint64_t* d_b,
+                    uint64_t* d_work, uint32_t n_polys, hx_stream_t stream);
+
 /* hx_ciphertext_step: the whole ciphertext tensor product (the computation of
  *   hx_ciphertext_tensor) on operands laid out back to back, with the
  *   operands kept: d_in holds a0 | a1 | b0 | b1 ([4][n_ct][limbs][N], in

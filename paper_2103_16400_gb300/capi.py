@@ -46,6 +46,7 @@ _SIGS = {
     "hx_ciphertext_tensor": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, VP],
     "hx_tensor_fma_inverse": [VP, VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U32, U32, VP],
     "hx_ciphertext_step": [VP, VP, VP, VP, P64, VP, U32, VP],
+    "hx_poly_product": [VP, VP, VP, VP, VP, U32, VP],
     "hx_dyadic_tensor_fma": [VP, VP, VP, VP, VP, VP, VP, P64, VP, VP, VP, U64, P64, U32, U32,
                              U32, VP],
     "hx_ragged_set_split": [U32, U32],
@@ -459,6 +460,12 @@ def hx_tensor_fma_inverse(plan, out0, out1, out2, A0, A1, B0, B1, scalars, e0, e
         _h(plan), ptr(out0), ptr(out1), ptr(out2), ptr(A0), ptr(A1), ptr(B0), ptr(B1),
         host_u64(scalars), ptr(e0), ptr(e1), ptr(e2), n_polys, input_mod_factor,
         _stream(stream)))
+
+
+def hx_poly_product(plan, result, a, b, work, n_polys: int = 1, stream=None):
+    """result = a * b in R_q, a and b kept; work: [2][n_polys][limbs][N] scratch."""
+    _check("hx_poly_product", load().hx_poly_product(
+        _h(plan), ptr(result), ptr(a), ptr(b), ptr(work), n_polys, _stream(stream)))
 
 
 def hx_ciphertext_step(plan, result, inputs, work, scalars, e, n_ct: int, stream=None):

@@ -325,6 +325,31 @@ int hx_tensor_fma_inverse(hx_plan_t plan, uint64_t* o0, uint64_t* o1, uint64_t* 
     return HX_OK;
 }
 
+int hx_poly_product(hx_plan_t plan, uint64_t* r, const uint64_t* a, const uint64_t* b,
+                    uint64_t* work, uint32_t n_polys, hx_stream_t stream) {
+    if (!plan || !r || !a || !b || !work) return HX_ERR_NULL;
+    if (n_polys == 0 || (uint64_t)n_polys * 2 * plan->n_limbs > (1ull << 31)) return HX_ERR_ARG;
+    if (!aligned16(r) || !aligned16(a) || !aligned16(b) || !aligned16(work)) return HX_ERR_ALIGN;
+    const uint64_t S = (uint64_t)n_polys * plan->n_limbs * plan->N;
+    const uintptr_t w = (uintptr_t)work, we = w + 2 * S * 8;
+    const uintptr_t spans[3][2] = {{(uintptr_t)r, (uintptr_t)r + S * 8},
+                                   {(uintptr_t)a, (uintptr_t)a + S * 8},
+                                   {(uintptr_t)b, (uintptr_t)b + S * 8}};
+    for (const auto& x : spans)
+        if (x[0] < we && w < x[1]) return HX_ERR_OVERLAP;
+    for (int k = 1; k < 3; ++k)   // the result: equal to an operand or apart from it
+        if (spans[0][0] != spans[k][0] && spans[0][0] < spans[k][1] && spans[k][0] < spans[0][1])
+            return HX_ERR_OVERLAP;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (mul_step_fusable(plan->cfg_fwd, plan->cfg_inv))
+        return cuda_status(
+            launch_mul_step(plan, r, a, b, work, n_polys, plan->cfg_fwd, plan->cfg_inv, s));
+    int st = hx_ntt_forward(plan, work, a, n_polys, 1, 4, stream);
+    if (st == HX_OK) st = hx_ntt_forward(plan, work + S, b, n_polys, 1, 4, stream);
+    if (st != HX_OK) return st;
+    return hx_dyadic_inverse(plan, r, work, work + S, n_polys, 4, stream);
+}
+
 int hx_ciphertext_step(hx_plan_t plan, uint64_t* r, const uint64_t* in, uint64_t* work,
                        const uint64_t* h_scalars, const uint64_t* e, uint32_t n_ct,
                        hx_stream_t stream) {

@@ -87,8 +87,8 @@ void count_launch(uint64_t n = 1);
 // (K1 for kind 3), 12-13 polynomials (outputs for the fused pass; for kind 3
 // bit 12 marks the tensor-fused inverse) per block, 14 staged twiddles,
 // 15-19 K2 (kind 3); for kind 0, bit 15 marks the inverse's first pass with
-// the dyadic product fused in; for kind 2, bit 16 marks the step kernel that
-// also runs the forward's row stages (ntt_ctrow.cu).
+// the dyadic product fused in; for kind 2, bit 16 marks the step kernels that
+// also run the forward's row stages (ntt_ctrow.cu), bit 17 the product's.
 uint32_t timing_begin(cudaStream_t s, uint32_t kernel);
 void timing_end(uint32_t slot, cudaStream_t s);
 
@@ -131,6 +131,15 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
 // schedules two-pass with the same row tiles (ct_step_fusable), else
 // cudaErrorNotSupported.
 bool ct_step_fusable(const NttCfg& f, const NttCfg& i);
+// The polynomial product in four launches: the forward's column pass of a
+// and of b (into work = a | b), the forward's row stages, the dyadic product
+// and the inverse's row stages in one kernel (work -> out, ntt_ctrow.cu), the
+// inverse's column pass.  Needs both schedules two-pass over the same split
+// (mul_step_fusable), else cudaErrorNotSupported.
+bool mul_step_fusable(const NttCfg& f, const NttCfg& i);
+cudaError_t launch_mul_step(const hx_plan_s* plan, uint64_t* out, const uint64_t* a,
+                            const uint64_t* b, uint64_t* work, uint32_t n_polys,
+                            const NttCfg& f, const NttCfg& i, cudaStream_t stream);
 cudaError_t launch_ct_step(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
                            uint64_t* work, const uint64_t* E, uint32_t n_ct,
                            const uint64_t* h_scalars, const NttCfg& f, const NttCfg& i,

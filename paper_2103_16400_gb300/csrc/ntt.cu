@@ -551,4 +551,66 @@ cudaError_t launch_ct_step(const hx_plan_s* plan, uint64_t* out, const uint64_t*
     // the inverse's column pass over the three outputs, N^-1 folded
     return launch_pass(plan, i.pass[0], out, out, 3 * n_ct, false, true, 1, stream);
 }
+
+// The product's step kernel runs the forward's and the inverse's row stages
+// in the inverse's row tiles: both schedules two-pass with the same split,
+// 8 elements a thread in both row passes.
+bool mul_step_fusable(const NttCfg& f, const NttCfg& i) {
+    if (f.npass != 2 || i.npass != 2 || is_cluster(f) || is_cluster(i)) return false;
+    const PassCfg& fr = f.pass[1];
+    const PassCfg& ir = i.pass[1];
+    if (fr.logGc != 0 || ir.logGc != 0 || fr.s0 != ir.s0 || fr.K != ir.K || fr.logR != 3 ||
+        ir.logR != 3)
+        return false;
+    if (!pick_mul_row(3, ir.K)) return false;
+    const int logT = ir.logGb + ir.K - 3;
+    return logT >= 5 && logT <= 9 &&
+           (size_t)8 * 2 * padded(1u << (ir.logGb + ir.K)) <= 192 * 1024;
+}
+
+cudaError_t launch_mul_step(const hx_plan_s* plan, uint64_t* out, const uint64_t* a,
+                            const uint64_t* b, uint64_t* work, uint32_t n_polys,
+                            const NttCfg& f, const NttCfg& i, cudaStream_t stream) {
+    if (!mul_step_fusable(f, i)) return cudaErrorNotSupported;
+    const int L = plan->logN;
+    const uint64_t S = (uint64_t)n_polys * plan->n_limbs << L;
+    // the forward's column pass over a, then b, into the two halves of work
+    cudaError_t e = launch_pass(plan, f.pass[0], work, a, n_polys, true, false, 4, stream);
+    if (e != cudaSuccess) return e;
+    e = launch_pass(plan, f.pass[0], work + S, b, n_polys, true, false, 4, stream);
+    if (e != cudaSuccess) return e;
+    const PassCfg& p = i.pass[1];
+    PassKernel k = pick_mul_row(3, p.K);
+    PassArgs args{};
+    args.out = out;
+    args.in = work;
+    args.limbs = plan->d_limbs;
+    args.order = plan->d_order;
+    args.n_limbs = plan->n_limbs;
+    args.n_polys = n_polys;
+    args.L = L;
+    args.s0 = p.s0;
+    args.logGb = p.logGb;
+    args.logGc = 0;
+    args.log_tiles_c = 0;
+    args.last = 0;
+    args.out_mf = 1;
+    const int logTE = p.logGb + p.K;
+    const uint32_t tiles = 1u << (L - logTE);
+    const size_t smem = (size_t)8 * 2 * padded(1u << logTE);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const uint32_t slot =
+        timing_begin(stream, 2u | (3u << 4) | ((uint32_t)p.K << 7) | (3u << 16));
+    k<<<dim3(tiles * n_polys, plan->n_limbs), 1u << (logTE - 3), smem, stream>>>(args);
+    timing_end(slot, stream);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the inverse's column pass, N^-1 folded
+    return launch_pass(plan, i.pass[0], out, out, n_polys, false, true, 1, stream);
+}
 }  // namespace hx

@@ -102,6 +102,92 @@ __global__ void __maxnreg__(HX_CTROW_MAXNREG) ntt_ct_row_kernel(PassArgs a, Tens
         ct_row_body<2, LOG_R, K>(sm, lc, cf, ci, t, tk, base, S, TEP);
 }
 
+// The polynomial product (Listing 4) the same way: one block per (row tile,
+// polynomial, limb) runs the forward's row stages on its tiles of a and b
+// (from the forward column pass's output, a.in = a | b back to back), forms
+// c_i = a_i b_i mod q in shared memory (mulmod_fused, the value
+// EltwiseMultMod gives) and runs the inverse's row stages on c, writing it for
+// the inverse's column pass.  Neither spectrum nor the product reaches HBM.
+#ifndef HX_MULROW_MAXNREG
+#define HX_MULROW_MAXNREG 64
+#endif
+
+template <int WC, int LOG_R, int K>
+__device__ __forceinline__ void mul_row_body(uint64_t* sm, const LimbDev& lc, TileCtx cf,
+                                             const TileCtx& ci, uint64_t S, uint32_t TEP) {
+    using Wd = typename std::conditional<WC == 0, uint32_t, uint64_t>::type;
+    constexpr int AR = WC == 1 ? 1 : 0;
+#pragma unroll 1
+    for (int o = 0; o < 2; ++o) {
+        ntt_rounds<true, false, Wd, AR, LOG_R, K, 0, 1, false>(sm + o * TEP, lc.fwd, lc, cf);
+        cf.gin += S;
+    }
+    __syncthreads();
+    const uint64_t q = lc.q, bk = lc.barrett_k;
+    const uint32_t Qm1 = lc.barrett_qm1;
+#pragma unroll 1
+    for (int it = 0; it < (1 << (LOG_R - 1)); ++it) {
+        const uint32_t l = pad(2 * (threadIdx.x + it * cf.nthreads));
+#pragma unroll
+        for (int h = 0; h < 2; ++h)   // the spectra are below 4q (the forward's out range)
+            sm[l + h] = mulmod_fused<WC>(small_mod_rt(sm[l + h], q, 4),
+                                         small_mod_rt(sm[TEP + l + h], q, 4), q, bk, Qm1);
+    }
+    __syncthreads();
+    ntt_rounds<false, false, Wd, AR, LOG_R, K, 0, 1, false>(sm, lc.inv, lc, ci);
+}
+
+// Grid (tiles x n_polys, limbs), 2^(logGb+K-LOG_R) threads, two padded tiles
+// of shared memory; a.n_polys products, a.s0 = L - K.
+template <int LOG_R, int K>
+__global__ void __maxnreg__(HX_MULROW_MAXNREG) ntt_mul_row_kernel(PassArgs a) {
+    extern __shared__ uint64_t sm[];
+    const uint32_t limb = a.order ? a.order[blockIdx.y] : blockIdx.y;
+    const uint32_t p = blockIdx.x % a.n_polys, tile = blockIdx.x / a.n_polys;
+    const LimbDev lc = a.limbs[limb];
+    const uint64_t S = ((uint64_t)a.n_polys * a.n_limbs) << a.L;   // elements per operand
+    const uint64_t row = ((uint64_t)p * a.n_limbs + limb) << a.L;
+    const uint32_t TE = 1u << (a.logGb + K);
+    TileCtx cf;
+    cf.gin = a.in + row;
+    cf.gout = nullptr;
+    cf.b_base = (uint64_t)tile << a.logGb;
+    cf.c_base = 0;
+    cf.L = a.L;
+    cf.s0 = a.s0;
+    cf.logGc = 0;
+    cf.logGb = a.logGb;
+    cf.w = 0;
+    cf.nthreads = TE >> LOG_R;
+    cf.out_mf = 4;
+    cf.last = true;
+    cf.poly_stride = S;
+    cf.np_valid = 1;
+    TileCtx ci = cf;
+    ci.gin = nullptr;
+    ci.gout = a.out + row;
+    ci.out_mf = a.out_mf;
+    ci.last = a.last != 0;
+    const uint32_t TEP = padded(TE);
+    if (lc.narrow)
+        mul_row_body<0, LOG_R, K>(sm, lc, cf, ci, S, TEP);
+    else if (lc.trunc)
+        mul_row_body<1, LOG_R, K>(sm, lc, cf, ci, S, TEP);
+    else
+        mul_row_body<2, LOG_R, K>(sm, lc, cf, ci, S, TEP);
+}
+
+PassKernel pick_mul_row(int logR, int K) {
+    if (logR != 3) return nullptr;
+    switch (K) {
+        case 6: return ntt_mul_row_kernel<3, 6>;
+        case 7: return ntt_mul_row_kernel<3, 7>;
+        case 8: return ntt_mul_row_kernel<3, 8>;
+        case 9: return ntt_mul_row_kernel<3, 9>;
+        default: return nullptr;
+    }
+}
+
 TensorPassKernel pick_ct_row(int logR, int K) {
     if (logR != 3) return nullptr;
     switch (K) {

@@ -924,6 +924,10 @@ typedef void (*MulPassKernel)(PassArgs, const uint64_t*, uint32_t);
 // the menu)
 MulPassKernel pick_mul_inv(int logR, int K, int np, bool tws);
 MulPassKernel pick_mul_inv_tws(int logR, int K, int np);
+// ntt_ctrow.cu: the product's step kernel (the forward's row stages on a and
+// b, the dyadic product, the inverse's row stages), 8 elements a thread, 6..9
+// stages; nullptr otherwise.
+PassKernel pick_mul_row(int logR, int K);
 
 // ntt_fwd.cu / ntt_inv.cu
 // ntt_f1.cu, ntt_f2.cu, ntt_i1.cu, ntt_i2.cu: plain kernels with 1 or 2

@@ -73,10 +73,10 @@ void timing_end(uint32_t slot, cudaStream_t s) {
         cudaEventRecord(g_tm[idx - 1].b, s);
 }
 
-static const char* kKernelNames[7] = {"ntt_pass_kernel",       "ntt_pipe_kernel",
+static const char* kKernelNames[8] = {"ntt_pass_kernel",       "ntt_pipe_kernel",
                                       "ntt_tensor_inv_kernel", "ntt_cluster_kernel",
                                       "ntt_cluster_tensor_kernel", "ntt_mul_inv_kernel",
-                                      "ntt_ct_row_kernel"};
+                                      "ntt_ct_row_kernel",     "ntt_mul_row_kernel"};
 
 template <int KIND>
 __global__ void __launch_bounds__(256) int_mul_probe_kernel(uint32_t iters, uint32_t a,
@@ -261,8 +261,8 @@ extern "C" int hx_kernel_name(uint32_t kernel, char* buf, uint32_t len) {
                      K, np, tws);
     else if (kind == 1)
         w = snprintf(buf, len, "%s<%u, %u, %u, %u>", kKernelNames[1], fwd, column, logR, K);
-    else if (kind == 2 && ((kernel >> 16) & 1u))   // forward rows, tensor, inverse rows
-        w = snprintf(buf, len, "%s<%u, %u>", kKernelNames[6], logR, K);
+    else if (kind == 2 && ((kernel >> 16) & 1u))   // forward rows, tensor or product, inverse rows
+        w = snprintf(buf, len, "%s<%u, %u>", kKernelNames[(kernel >> 17) & 1u ? 7 : 6], logR, K);
     else if (kind == 2)
         w = snprintf(buf, len, "%s<%u, %u, %u, %u>", kKernelNames[2], logR, K, tws, np);
     else if ((kernel >> 12) & 1u)   // cluster-fused: K holds K1, bits 15-19 K2

@@ -238,11 +238,10 @@ class Server:
     def _launch_direct(self, reqs: List["Request"], sid: int, need: int,
                        on_caller_stream: bool = False) -> dict:
         """HBM-resident requests through the per-request calls, one after
-        another on one stream (no descriptor lists): a product transforms a
-        and b out of place into a workspace kept per stream (requests on one
-        stream reuse it in order), then hx_dyadic_inverse (the product inside
-        the inverse's first pass) writes its result; a transform writes its
-        result directly.  on_caller_stream: the idle path -- the submitting
+        another on one stream (no descriptor lists): a product is one
+        hx_poly_product call (a and b kept; their spectra in a workspace kept
+        per stream, which requests on one stream reuse in order); a transform
+        writes its result directly.  on_caller_stream: the idle path -- the submitting
         thread's current stream (as a direct call would run; the server is
         idle, so the idle path's workspace and event are free), waited on by
         spinning in the driver; else server stream `sid`."""
@@ -268,11 +267,11 @@ class Server:
                 if plan is None:
                     plan = self.plan(r.N, r.moduli)
                 if r.op == "mul":
-                    wb = wa + 8 * words
-                    capi.hx_ntt_forward(plan, wa, r.a, 1, 1, 4, sh)
-                    capi.hx_ntt_forward(plan, wb, r.b, 1, 1, 4, sh)
-                    capi.hx_dyadic_inverse(plan, out, wa, wb, 1, 4, sh)
-                    launches += 3
+                    # both spectra in the workspace, the product inside the
+                    # inverse (four launches where the plan's schedules
+                    # share their row passes)
+                    capi.hx_poly_product(plan, out, r.a, r.b, wa, 1, sh)
+                    launches += 1
                 else:
                     (capi.hx_ntt_forward if r.op == "fwd" else capi.hx_ntt_inverse)(
                         plan, out, r.a, 1, 1, 1, sh)
