@@ -129,29 +129,29 @@ def kernel_source_hash():
 #: capture commands.
 TRAFFIC_BYTES = {
     ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
-     "ad1c7d1e134c893b"): 67254016 + 17140224 + 100653056 + 14171648,
+     "90e86c4be3dbf0a3"): 67255040 + 16992000 + 100655616 + 14094336,
     ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]",
-     "ad1c7d1e134c893b"): 67318528 + 22884864 + 100587520 + 14384384,
+     "90e86c4be3dbf0a3"): 67320064 + 22632960 + 100588288 + 13694976,
     ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]",
-     "ad1c7d1e134c893b"): 67336960 + 22652416 + 100587008 + 13977856,
+     "90e86c4be3dbf0a3"): 67317760 + 22569472 + 100588032 + 13873152,
     ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
-     "ad1c7d1e134c893b"): 67252480 + 22662400 + 100652288 + 14222848,
+     "90e86c4be3dbf0a3"): 67258368 + 22800128 + 100655360 + 14037760,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "ad1c7d1e134c893b"): 151007744 + 20687360,
+     "90e86c4be3dbf0a3"): 151015168 + 20824576,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "ad1c7d1e134c893b"): 151004928 + 20776448,
+     "90e86c4be3dbf0a3"): 151014400 + 20473600,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "ad1c7d1e134c893b"): 151005184 + 20725760,
+     "90e86c4be3dbf0a3"): 151015424 + 20709632,
     ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "ad1c7d1e134c893b"): 184721920 + 26239488,
+     "90e86c4be3dbf0a3"): 184724480 + 26259712,
     ("ntt_ct_row_kernel<3, 8>", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 2]]",
-     "ad1c7d1e134c893b"): 184366592 + 26547200,
+     "90e86c4be3dbf0a3"): 184422912 + 26591232,
     ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "ad1c7d1e134c893b"): 184759808 + 26149376,
+     "90e86c4be3dbf0a3"): 184783616 + 26323456,
     ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "ad1c7d1e134c893b"): 184722432 + 26258688,
+     "90e86c4be3dbf0a3"): 184726016 + 26173184,
     ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "ad1c7d1e134c893b"): 184761088 + 26358272,
+     "90e86c4be3dbf0a3"): 184731904 + 26259968,
 }
 
 
