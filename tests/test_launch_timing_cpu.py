@@ -20,6 +20,7 @@ def test_kernel_names():
     assert capi.hx_kernel_name(kid(1, 1, 0, 3, 9)) == "ntt_pipe_kernel<1, 0, 3, 9>"
     assert capi.hx_kernel_name(kid(2, 0, 0, 3, 9, 3)) == "ntt_tensor_inv_kernel<3, 9, 0, 3>"
     assert capi.hx_kernel_name(kid(2, 0, 0, 3, 9, 0) | 1 << 16) == "ntt_ct_row_kernel<3, 9>"
+    assert capi.hx_kernel_name(kid(2, 0, 0, 3, 8, 0) | 3 << 16) == "ntt_mul_row_kernel<3, 8>"
     # cluster-fused transforms: kind 3, K1 in the K field, K2 in bits 15-19
     assert capi.hx_kernel_name(kid(3, 1, 0, 4, 8, 0) | 8 << 15) == "ntt_cluster_kernel<1, 4, 8, 8>"
     assert (capi.hx_kernel_name(kid(3, 0, 0, 4, 7, 1) | 9 << 15)
@@ -155,3 +156,14 @@ def test_step_kernel_work_is_both_row_passes_and_the_tensor():
     ops = bench.kernel_slots(step, N, moduli, per_butterfly=bench.ops_per_butterfly)
     assert ops == 7 * 9 * (N // 2) * (21 * 10 + 11 * 3)
     assert bench.kernel_bytes(step, N, 32) == bench.kernel_bytes(kid(2, 0, 0, 3, 9, 3), N, 32)
+
+
+def test_product_step_kernel_work():
+    """The product's step kernel: the forward's row stages on a and b and the
+    inverse's on their product (three polynomials' worth of row stages);
+    a and b in, a b out."""
+    N, moduli = 1 << 16, W.mixed_width_primes(32)
+    mul = kid(2, 0, 0, 3, 8, 0) | 3 << 16
+    row_inv = bench.kernel_slots(kid(0, 0, 0, 3, 8), N, moduli)       # three polynomials
+    assert bench.kernel_slots(mul, N, moduli) == row_inv
+    assert bench.kernel_bytes(mul, N, 32) == 3 * 8 * N * 32
