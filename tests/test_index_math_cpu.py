@@ -265,3 +265,30 @@ def test_ragged_menu_passes(L):
         assert p.logTE == min(L, 11) and p.T == 256     # 256 threads, 2048 elements (1024 at 2^10)
         test_tiles_cover_the_transform_once(p)
         test_rounds_registers_butterflies_and_twiddles(p)
+
+
+@pytest.mark.parametrize("logTE", range(8, 13))
+@pytest.mark.parametrize("tiles", [2, 4])
+def test_step_kernels_element_wise_step_covers_each_tile_once(logTE, tiles):
+    """The step kernels' element-wise step (the tensor, or the product): with
+    8 elements a thread and TE >> 3 threads, thread t at step it handles
+    positions 2i and 2i + 1, i = t + it * threads, it < 4, reading and
+    writing tile k at k * padded(TE) + pad(2i) (+ 1): every position of every
+    tile exactly once, inside its own tile, with the pair in one 16-word row
+    (pad(2i) + 1 = pad(2i + 1))."""
+    TE = 1 << logTE
+    threads = TE >> 3
+    padded = TE + TE // 16
+    seen = [set() for _ in range(tiles)]
+    for t in range(threads):
+        for it in range(4):
+            i = t + it * threads
+            l = pad(2 * i)
+            assert l + 1 == pad(2 * i + 1) and l + 1 < padded
+            for k in range(tiles):
+                for h in (0, 1):
+                    off = k * padded + l + h
+                    assert k * padded <= off < (k + 1) * padded
+                    assert 2 * i + h not in seen[k]
+                    seen[k].add(2 * i + h)
+    assert all(s == set(range(TE)) for s in seen)
