@@ -129,29 +129,29 @@ def kernel_source_hash():
 #: capture commands.
 TRAFFIC_BYTES = {
     ("forward_call", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
-     "90e86c4be3dbf0a3"): 67255040 + 16992000 + 100655616 + 14094336,
+     "4117db26c6aea96b"): 67256064 + 16780800 + 100656128 + 13868288,
     ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 1]]",
-     "90e86c4be3dbf0a3"): 67320064 + 22632960 + 100588288 + 13694976,
+     "4117db26c6aea96b"): 67320064 + 22699776 + 100587776 + 13716992,
     ("forward_call", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 2, 0, 3, 0, 1]]",
-     "90e86c4be3dbf0a3"): 67317760 + 22569472 + 100588032 + 13873152,
+     "4117db26c6aea96b"): 67319808 + 22932992 + 100590080 + 13775616,
     ("forward_call", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 1]]",
-     "90e86c4be3dbf0a3"): 67258368 + 22800128 + 100655360 + 14037760,
+     "4117db26c6aea96b"): 67253760 + 23036160 + 100656640 + 13927680,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "90e86c4be3dbf0a3"): 151015168 + 20824576,
+     "4117db26c6aea96b"): 151037696 + 20775680,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "90e86c4be3dbf0a3"): 151014400 + 20473600,
+     "4117db26c6aea96b"): 151021568 + 20788224,
     ("ntt_tensor_inv_kernel<3, 9, 0, 3>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "90e86c4be3dbf0a3"): 151015424 + 20709632,
+     "4117db26c6aea96b"): 151013632 + 20402688,
     ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "90e86c4be3dbf0a3"): 184724480 + 26259712,
+     "4117db26c6aea96b"): 184727552 + 26205696,
     ("ntt_ct_row_kernel<3, 8>", "[[0, 8, 0, 3, 4, 0, 1], [8, 8, 1, 0, 3, 0, 2]]",
-     "90e86c4be3dbf0a3"): 184422912 + 26591232,
+     "4117db26c6aea96b"): 184367360 + 26626304,
     ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 0, 1], [7, 9, 0, 0, 3, 0, 2]]",
-     "90e86c4be3dbf0a3"): 184783616 + 26323456,
+     "4117db26c6aea96b"): 184738304 + 26228992,
     ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 4, 4, 2, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "90e86c4be3dbf0a3"): 184726016 + 26173184,
+     "4117db26c6aea96b"): 184725248 + 26214400,
     ("ntt_ct_row_kernel<3, 9>", "[[0, 7, 0, 3, 4, 0, 1], [7, 9, 1, 0, 3, 0, 2]]",
-     "90e86c4be3dbf0a3"): 184731904 + 26259968,
+     "4117db26c6aea96b"): 184711936 + 26242304,
 }
 
 

@@ -318,8 +318,9 @@ int hx_poly_product(hx_plan_t plan, uint64_t* d_result, const uint64_t* d_a, con
  *     d2 = A1 B1,  A_i, B_i = NTT(a_i, b_i)           (Section 2.2, Listing 4)
  *   d_work ([4][n_ct][limbs][N]) is scratch the caller provides; it may equal
  *   d_in (the operands are then overwritten).  When the plan's forward and
- *   inverse schedules are both two-pass with the same row tiles (8 elements a
- *   thread, 6..9 row stages), the call is three launches: the forward's column
+ *   inverse schedules are both two-pass with row passes over the same stages
+ *   (8 elements a thread, 6..9 row stages; the inverse's row tile is used for
+ *   both), the call is three launches: the forward's column
  *   pass, one kernel that runs the forward's row stages on the four operands,
  *   the tensor step and the inverse's row stages on the three outputs with
  *   the spectra kept in shared memory (they never reach HBM), and the

@@ -128,8 +128,8 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
 // (in -> work, the four operands back to back), the forward's row stages,
 // the tensor and the inverse's row stages in one kernel (work, E -> out,
 // ntt_ctrow.cu), the inverse's column pass (out, in place).  Needs both
-// schedules two-pass with the same row tiles (ct_step_fusable), else
-// cudaErrorNotSupported.
+// schedules two-pass with row passes over the same stages (ct_step_fusable;
+// the inverse's row tile serves both), else cudaErrorNotSupported.
 bool ct_step_fusable(const NttCfg& f, const NttCfg& i);
 // The polynomial product in four launches: the forward's column pass of a
 // and of b (into work = a | b), the forward's row stages, the dyadic product

@@ -480,17 +480,19 @@ cudaError_t launch_tensor_inverse(const hx_plan_s* plan, uint64_t* out, const ui
 
 
 // The step's two row passes fused around the tensor (ntt_ctrow.cu): both
-// schedules two-pass, their row passes over the same stages in the same row
-// tiles with 8 elements a thread.
+// schedules two-pass, their row passes over the same stages with 8 elements
+// a thread; the kernel runs both in the inverse's row tiles.
 bool ct_step_fusable(const NttCfg& f, const NttCfg& i) {
     if (f.npass != 2 || i.npass != 2 || is_cluster(f) || is_cluster(i)) return false;
     const PassCfg& fr = f.pass[1];
     const PassCfg& ir = i.pass[1];
-    if (fr.logGc != 0 || ir.logGc != 0 || fr.s0 != ir.s0 || fr.K != ir.K ||
-        fr.logGb != ir.logGb || fr.logR != 3 || ir.logR != 3)
+    if (fr.logGc != 0 || ir.logGc != 0 || fr.s0 != ir.s0 || fr.K != ir.K || fr.logR != 3 ||
+        ir.logR != 3)
         return false;
-    if (!pick_ct_row(3, fr.K)) return false;
-    return (size_t)8 * 4 * padded(1u << (fr.logGb + fr.K)) <= 192 * 1024;
+    if (!pick_ct_row(3, ir.K)) return false;
+    const int logT = ir.logGb + ir.K - 3;
+    return logT >= 5 && logT <= 9 &&
+           (size_t)8 * 4 * padded(1u << (ir.logGb + ir.K)) <= 192 * 1024;
 }
 
 cudaError_t launch_ct_step(const hx_plan_s* plan, uint64_t* out, const uint64_t* in,
@@ -502,7 +504,7 @@ cudaError_t launch_ct_step(const hx_plan_s* plan, uint64_t* out, const uint64_t*
     // the forward's column pass over the four operands
     cudaError_t e = launch_pass(plan, f.pass[0], work, in, 4 * n_ct, true, false, 4, stream);
     if (e != cudaSuccess) return e;
-    const PassCfg& p = f.pass[1];
+    const PassCfg& p = i.pass[1];   // the row tile of both directions
     TensorPassKernel k = pick_ct_row(3, p.K);
     PassArgs a{};
     a.out = out;

@@ -63,6 +63,22 @@ def test_three_launch_step_matches_oracle(hexlib, logN, K1, logGb, n_limbs, n_ct
         np.testing.assert_array_equal(g, e)
 
 
+def test_default_schedules_take_the_three_launch_form(hexlib):
+    """The plan's default schedules at N = 2^16 have row passes over the same
+    stages in different row tiles (forward one row, inverse two): the step
+    kernel runs both in the inverse's tiles."""
+    N, n_ct = 1 << 16, 1
+    moduli = W.mixed_width_primes(4)
+    ins, es, s = inputs(W.SEED_BASE + 940, n_ct, moduli, N)
+    plan = capi.Plan(N, moduli)
+    f, i = plan.schedule(plan.FORWARD), plan.schedule(plan.INVERSE)
+    assert f[1][:2] == i[1][:2] and f[1][2] != i[1][2]
+    got, launches = run(plan, ins, es, s, n_ct)
+    assert launches == 3
+    for g, e in zip(got, expected(ins, es, s, moduli)):
+        np.testing.assert_array_equal(g, e)
+
+
 def test_in_place_and_many_limbs(hexlib):
     """70 limbs (two launches of the fused kernel) with the operands
     transformed in place; the inputs are then the forward column pass's
